@@ -1,0 +1,147 @@
+"""Seeded synthetic initial conditions shared by the tests, the oracle runs and
+the benchmark.
+
+This module holds only problem set-ups (closed-form initial fields and seeded
+random parameters); none of the scheme's arithmetic lives here.  All arrays are
+NumPy float64 in [z][y][x] / [y][x] order (x fastest), in lattice units
+(delta_x = 1).  Density is absolute; ``p = rho c_s^2`` (Section 2).
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+BATCH_SEED = 20201207
+TURB_TRAIN_SEEDS = range(0, 200)
+TURB_TEST_SEEDS = range(1000, 1020)
+
+
+def cs2_of(dt: float) -> float:
+    """c = delta_x / delta_t with delta_x = 1, c_s^2 = c^2 / 3 (Section 2)."""
+    return (1.0 / dt) ** 2 / 3.0
+
+
+def tgv2d(n: int, u0: float, dt: float = 1.0, rho0: float = 1.0, x0: float = 0.0):
+    """2D Taylor-Green vortex on an n x n periodic grid, wavenumber k = 2 pi / n
+    (the paper's Eqs. 3.1a-c with L = n/2 lattice units, evaluated at t = 0):
+      u = -u0 cos(kx) sin(ky), v = u0 sin(kx) cos(ky),
+      p = p0 - rho0 u0^2/4 (cos 2kx + cos 2ky),  rho = p / c_s^2, p0 = rho0 c_s^2.
+    ``x0`` shifts the node positions (x_i = x0 + i)."""
+    k = 2.0 * np.pi / n
+    x = x0 + np.arange(n, dtype=np.float64)
+    X, Y = np.meshgrid(x, x, indexing="xy")  # arrays [y][x]
+    u = -u0 * np.cos(k * X) * np.sin(k * Y)
+    v = u0 * np.sin(k * X) * np.cos(k * Y)
+    rho = rho0 - rho0 * u0 * u0 / (4.0 * cs2_of(dt)) * (np.cos(2 * k * X) + np.cos(2 * k * Y))
+    return rho, u, v
+
+
+def tgv2d_exact(n: int, u0: float, nu: float, t: float, x0: float = 0.0):
+    """Closed-form velocity of the 2D TGV at time t (decay exp(-2 nu k^2 t))."""
+    k = 2.0 * np.pi / n
+    x = x0 + np.arange(n, dtype=np.float64)
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    f = np.exp(-2.0 * nu * k * k * t)
+    return -u0 * np.cos(k * X) * np.sin(k * Y) * f, u0 * np.sin(k * X) * np.cos(k * Y) * f
+
+
+def tgv3d(n: int, u0: float, dt: float = 1.0, rho0: float = 1.0):
+    """Standard 3D Taylor-Green vortex on an n^3 periodic grid, k = 2 pi / n:
+      u = u0 sin(kx) cos(ky) cos(kz), v = -u0 cos(kx) sin(ky) cos(kz), w = 0,
+      p = p0 + rho0 u0^2/16 (cos 2kx + cos 2ky)(cos 2kz + 2).
+    Arrays are [z][y][x]."""
+    k = 2.0 * np.pi / n
+    x = np.arange(n, dtype=np.float64) * k
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    u = u0 * np.sin(X) * np.cos(Y) * np.cos(Z)
+    v = -u0 * np.cos(X) * np.sin(Y) * np.cos(Z)
+    w = np.zeros_like(u)
+    rho = rho0 + rho0 * u0 * u0 / (16.0 * cs2_of(dt)) * (np.cos(2 * X) + np.cos(2 * Y)) * (
+        np.cos(2 * Z) + 2.0)
+    return rho, u, v, w
+
+
+def tgv3d_nu(n: int, u0: float, re: float) -> float:
+    """nu for Re = u0 L / nu with L = n / (2 pi) lattice units."""
+    return u0 * (n / (2.0 * np.pi)) / re
+
+
+def cavity2d(n: int, lid: float):
+    """Lid-driven cavity at rest (u = v = 0, rho = 1) with the lid row moving."""
+    rho = np.ones((n, n))
+    u = np.zeros((n, n))
+    v = np.zeros((n, n))
+    u[-1, 1:-1] = lid
+    return rho, u, v
+
+
+def cavity_nu(n: int, lid: float, re: float) -> float:
+    """nu = U_lid L / Re with the wall-to-wall length L = n - 1."""
+    return lid * (n - 1) / re
+
+
+def drop2d(n: int, radius: float, W: float = 4.0, eps: float = 0.0, cx=None, cy=None):
+    """phi = -tanh(2 (r - R(theta)) / W) with R(theta) = R (1 + eps cos 2 theta):
+    +1 inside the drop, -1 outside.  Fluid at rest, rho = 1."""
+    cx = (n - 1) / 2.0 if cx is None else cx
+    cy = (n - 1) / 2.0 if cy is None else cy
+    x = np.arange(n, dtype=np.float64)
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    dx, dy = X - cx, Y - cy
+    r = np.hypot(dx, dy)
+    th = np.arctan2(dy, dx)
+    rt = radius * (1.0 + eps * np.cos(2.0 * th))
+    phi = -np.tanh(2.0 * (r - rt) / W)
+    return np.ones((n, n)), np.zeros((n, n)), np.zeros((n, n)), phi
+
+
+@dataclasses.dataclass
+class DropRun:
+    n: int
+    radius: float
+    eps: float
+    sigma: float
+    W: float = 4.0
+    nu: float = 0.1
+    M: float = 0.1
+
+
+def batch_drops(nruns: int = 512, seed: int = BATCH_SEED, nmin: int = 64, nmax: int = 512):
+    """Seeded parameters of the batched static/oscillating drop workload:
+    grid side N uniform in [nmin, nmax], R = r N with r ~ U[0.15, 0.35],
+    elliptical perturbation eps ~ U[0, 0.10], sigma log-uniform in [1e-4, 1e-2],
+    W = 4, nu = 0.1, M = 0.1 (lattice units)."""
+    rng = np.random.default_rng(seed)
+    runs = []
+    for _ in range(nruns):
+        n = int(rng.integers(nmin, nmax + 1))
+        r = float(rng.uniform(0.15, 0.35))
+        eps = float(rng.uniform(0.0, 0.10))
+        sigma = float(10.0 ** rng.uniform(-4.0, -2.0))
+        runs.append(DropRun(n=n, radius=r * n, eps=eps, sigma=sigma))
+    return runs
+
+
+def turbulence2d(n: int, seed: int, u_rms: float = 0.05, k0: float = 8.0):
+    """Decaying-turbulence initial field: stream function with random phases and
+    energy spectrum E(k) ~ k^4 exp(-2 (k/k0)^2) (k in units of the box
+    wavenumber), u = d psi/dy, v = -d psi/dx (divergence free), scaled to the
+    requested u_rms, rho = 1."""
+    rng = np.random.default_rng(seed)
+    kx = np.fft.fftfreq(n) * n
+    KX, KY = np.meshgrid(kx, kx, indexing="xy")
+    kk = np.hypot(KX, KY)
+    kk[0, 0] = 1.0
+    ek = kk ** 4 * np.exp(-2.0 * (kk / k0) ** 2)
+    # |u_hat|^2 ~ E(k) / (pi k) on the 2D shell -> |psi_hat| = |u_hat| / k
+    amp = np.sqrt(ek / (np.pi * kk)) / kk
+    amp[0, 0] = 0.0
+    phase = np.exp(2j * np.pi * rng.random((n, n)))
+    psi_hat = amp * phase
+    kxs = 2.0 * np.pi * KX / n
+    kys = 2.0 * np.pi * KY / n
+    u = np.real(np.fft.ifft2(1j * kys * psi_hat))
+    v = np.real(np.fft.ifft2(-1j * kxs * psi_hat))
+    s = u_rms / np.sqrt(np.mean(u * u + v * v))
+    return np.ones((n, n)), u * s, v * s
