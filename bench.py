@@ -1,0 +1,323 @@
+#!/usr/bin/env python3
+"""Benchmark of the fused SMAME time step on one GB300.
+
+Workload (the configuration the GLUPS / %-of-HBM-roofline metric is quoted
+on): 3D periodic Taylor-Green vortex, 256^3 nodes, u0 = 0.05, Re = 1600
+(nu = u0 (256 / 2 pi) / 1600), fields stored and updated in FP32 deviation
+form (rho - rho0, u, v, w), FP64 diagnostics.  One bench step = one time step
+of Eqs. (2.10)-(2.11) = one launch of the fused 3D kernel.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the CPU oracle (the
+reference arm of this project) on a bounded sample of the same workload.
+Under torchrun with N > 1 every rank advances its own independent replica of
+the workload (no data exchange; weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N3 = 256
+U0 = 0.05
+RE = 1600.0
+BYTES_PER_LU_FP32 = 32      # 4 fields read + 4 fields written, 4 B each
+WORKLOAD = ("3D periodic Taylor-Green vortex 256^3, u0=0.05, Re=1600, "
+            "FP32 deviation storage, FP64 reductions")
+PROFILE = os.path.join(ROOT, "profiles", "step3d_fp32_tgv256.md")
+KERNEL_SRC = os.path.join(ROOT, "paper_2012_03525_gb300", "csrc", "acm_step3d.cu")
+
+
+def env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+class ClockSampler:
+    """Samples nvidia-smi SM clocks and throttle reasons during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the 3D step kernel from the committed ncu
+    summary, if it was taken on the current kernel source (else None)."""
+    try:
+        txt = open(PROFILE).read()
+        src_hash = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    vals = {}
+    for ln in txt.splitlines():
+        if ":" in ln and ln.strip().startswith("- "):
+            k, v = ln.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_sha256_16") != src_hash:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch_full_256"])
+    except (KeyError, ValueError):
+        return None
+
+
+def cpu_baseline(seconds: float = 12.0):
+    """Time the CPU oracle (single thread) on z-slabs of the 256^3 workload."""
+    import numpy as np
+    from oracle import c_oracle as co
+    from paper_2012_03525_gb300 import workloads as wl
+    nu = wl.tgv3d_nu(N3, U0, RE)
+    rho, u, v, w = wl.tgv3d(N3, U0)
+    nz = 8
+    sl = [np.ascontiguousarray(x[:nz]) for x in (rho, u, v, w)]
+    p = co.make_params((nz, N3, N3), nu=nu)
+    co.step(p, *sl, nsteps=1)  # warm (builds the .so)
+    steps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        co.step(p, *sl, nsteps=1)
+        steps += 1
+    dt = time.perf_counter() - t0
+    lu = nz * N3 * N3 * steps
+    return {"value": lu / dt / 1e9, "unit": "GLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"{steps} steps of a {nz}x{N3}x{N3} periodic slab of the 256^3 TGV, "
+                      f"FP64 C oracle, single thread, {dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import numpy as np
+    from oracle import c_oracle as co
+    from paper_2012_03525_gb300 import workloads as wl
+    budget = 150.0  # seconds for warmup + steps
+    per_step = budget / max(1, args.steps + args.warmup)
+    nz = max(1, min(N3, int(per_step * 6e6 / (N3 * N3))))
+    nu = wl.tgv3d_nu(N3, U0, RE)
+    rho, u, v, w = wl.tgv3d(N3, U0)
+    sl = [np.ascontiguousarray(x[:nz]) for x in (rho, u, v, w)]
+    p = co.make_params((nz, N3, N3), nu=nu)
+    for _ in range(args.warmup):
+        co.step(p, *sl, nsteps=1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        co.step(p, *sl, nsteps=1)
+    dt = time.perf_counter() - t0
+    lu = nz * N3 * N3 * args.steps
+    val = lu / dt / 1e9
+    sample = (f"each step: one oracle step on a {nz}x{N3}x{N3} periodic slab of the 256^3 TGV "
+              f"(FP64 C oracle, single thread)")
+    print(json.dumps({
+        "metric": "GLUPS", "value": val, "unit": "GLUPS", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "impl": "reference",
+        "config": {"workload": WORKLOAD, "nodes_per_step": lu // args.steps},
+        "cpu_baseline": {"value": val, "unit": "GLUPS", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": val, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--zchunks", type=int, default=env_int("ACM_ZCHUNKS", 0))
+    ap.add_argument("--t3y", type=int, default=env_int("ACM_T3Y", 8))
+    ap.add_argument("--n", type=int, default=N3,
+                    help="grid side (profiling runs use a smaller cube; the bench line is 256)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+    from paper_2012_03525_gb300 import acm, build
+    from paper_2012_03525_gb300 import workloads as wl
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+
+    n3 = args.n
+    nu = wl.tgv3d_nu(n3, U0, RE)
+    rho, u, v, w = wl.tgv3d(n3, U0)
+    nodes = n3 ** 3
+    mass0 = float(rho.sum())
+    prm = acm.make_params((n3, n3, n3), nu=nu, precision=acm.FP32_DEV)
+    solver = acm.Solver(prm)
+    stream = torch.cuda.Stream()
+    solver.set_stream(stream.cuda_stream)
+    if args.zchunks:
+        solver.set_tuning(acm.TUNE_ZCHUNKS, args.zchunks)
+    solver.set_tuning(acm.TUNE_T3Y, args.t3y)
+    solver.set_fields(rho, u, v, w)
+    solver.step(args.warmup)
+    solver.sync()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        ev0.record(stream)
+        solver.step(args.steps)
+        ev1.record(stream)
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    solver.sync()  # raises on blow-up
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    diag = solver.reduce()
+
+    # end to end through the C ABI with pinned host buffers: upload the initial
+    # state, run the same K steps, read the diagnostics and the final fields
+    pinned = [torch.from_numpy(x).pin_memory() for x in (rho, u, v, w)]
+    outs = [torch.empty(x.shape, dtype=torch.float64).pin_memory() for x in (rho, u, v, w)]
+    barrier()
+    t0 = time.perf_counter()
+    solver.set_fields_raw(0, [p.data_ptr() for p in pinned] + [None])
+    solver.step(args.steps)
+    diag_e2e = solver.reduce()
+    solver.fields_raw(0, [o.data_ptr() for o in outs] + [None])
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    if rank != 0:
+        solver.close()
+        dist.destroy_process_group()
+        return 0
+
+    glups = nodes * args.steps * world / (ms / 1e3) / 1e9
+    per_launch_s = ms / 1e3 / args.steps
+    peak, peak_kind = measured_peaks()
+    achieved = BYTES_PER_LU_FP32 * nodes / per_launch_s / 1e9
+    h2d = 4 * nodes * 8
+    d2h = 4 * nodes * 8 + 8 * 8
+    out = {
+        "metric": "GLUPS", "value": glups, "unit": "GLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD if n3 == N3 else WORKLOAD.replace("256^3", f"{n3}^3"),
+                   "nodes": nodes, "grid": [n3, n3, n3],
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (2 x 268 MB state vs 129 MB L2), no flush",
+                   "zchunks": args.zchunks or "heuristic", "t3y": args.t3y,
+                   "graph_steps": 64},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": f"{peak_kind} copy bandwidth",
+                     "traffic": profiled_traffic(),
+                     "algorithmic_bytes_per_launch": BYTES_PER_LU_FP32 * nodes},
+        "e2e": {"value": nodes * args.steps * world / e2e_s / 1e9, "unit": "GLUPS",
+                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+                "seconds": e2e_s},
+        "gpu_launches": args.steps,
+        "clocks": clk.summary(),
+        "diagnostics": {"mass_rel_drift": float(max(abs(diag[0] - mass0),
+                                                    abs(diag_e2e[0] - mass0)) / mass0),
+                        "E_k": float(diag[4]), "max_u": float(diag[6]),
+                        "nonfinite": float(diag[7])},
+    }
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(out))
+    solver.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,173 @@
+/*
+ * acm.h -- C ABI of libacm, a GB300 (sm_103a) solver for the simplified
+ * "more actual macroscopic equations" (SMAMEs) of Huang, "Towards the simplest
+ * simulation of incompressible viscous flows inspired by the lattice Boltzmann
+ * method" (arXiv:2012.03525).
+ *
+ * One time step advances density (pressure p = rho c_s^2) and velocity on a
+ * collocated uniform grid (Section 2):
+ *   Eq. (2.10)  rho^{n+1} = rho^n - dt d_a(rho u_a)^n + 1/2 c_s^2 dt^2 d_aa rho^n
+ *   Eq. (2.11)  (rho u_a)^{n+1} = (rho u_a)^n - dt d_b(rho u_a u_b + rho c_s^2 delta_ab)^n
+ *               + nu dt d_bb(rho u_a)^n - (nu + 1/2 c_s^2 dt)(d_a rho^{n+1} - d_a rho^n)
+ *               + dt rho^{n+1} g_a                 (body force, Section 2)
+ *               + dt F_ST,a, F_ST = -phi d_a mu    (two-phase, Section 2)
+ * with second-order centred differences (Eqs. 2.12-2.13).  The two-phase
+ * order parameter phi follows the Cahn-Hilliard equation (Eq. 2.14) with
+ * mu = 4 a phi (phi^2 - 1) - kappa d_aa phi, a = 3 sigma / (4W),
+ * kappa = 3 sigma W / 8, discretised with lattice-weighted isotropic
+ * (D2Q9) operators and advanced by a two-stage (Heun) Runge-Kutta step.
+ *
+ * Units: lattice units with delta_x = 1 and delta_t = params.dt, so the
+ * lattice speed is c = 1/dt and c_s^2 = c^2/3 (Section 2, after Eq. 2.1).
+ *
+ * Conventions for every call:
+ *   - every function returns an acm_status; nothing throws across the ABI;
+ *   - host arrays are caller-owned, contiguous, [z][y][x] with x fastest,
+ *     nx*ny*nz doubles per field; NULL is allowed for fields a run does not
+ *     have (w in 2D, phi in single-phase runs) and, for acm_fields, for any
+ *     field the caller does not want;
+ *   - device memory belongs to the handle; the solver's arithmetic runs only
+ *     on the GPU -- there is no CPU path;
+ *   - acm_step is asynchronous on the handle's stream; a numerical blow-up
+ *     (non-finite value) detected by the step kernels is reported as
+ *     ACM_EUNSTABLE by the next synchronising call (acm_sync, acm_fields,
+ *     acm_reduce_mass) and stays sticky until acm_set_fields;
+ *   - a handle may be used by one host thread at a time.
+ */
+#ifndef ACM_H
+#define ACM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct acm_handle acm_handle;
+
+typedef enum {
+    ACM_OK = 0,
+    ACM_EINVAL = -1,    /* invalid argument or unsupported combination */
+    ACM_ENOMEM = -2,    /* device or host allocation failed */
+    ACM_ECUDA = -3,     /* a CUDA runtime/driver call failed */
+    ACM_EUNSTABLE = -4, /* a non-finite value appeared in the fields */
+    ACM_ETIMEOUT = -5,  /* a bounded device-side wait gave up */
+    ACM_ESTATE = -6     /* call out of order (e.g. step before set_fields) */
+} acm_status;
+
+/* boundary condition of one face */
+enum { ACM_BC_PERIODIC = 0, ACM_BC_WALL = 1, ACM_BC_LID = 2 };
+
+/* storage/arithmetic precision of the fields */
+enum {
+    ACM_FP64 = 0,     /* rho - rho0 and u stored and updated in FP64 */
+    ACM_FP32_DEV = 1  /* rho - rho0 and u stored and updated in FP32 (deviation
+                         form: the O(Ma^2) density signal keeps its digits) */
+};
+
+typedef struct {
+    int dim;            /* 2 or 3 */
+    int nx, ny, nz;     /* nodes per direction (nz = 1 in 2D); periodic faces
+                           have no duplicated end node, wall faces put the
+                           wall on the first/last node */
+    double dt;          /* delta_t in lattice units (delta_x = 1); c_s^2 = 1/(3 dt^2) */
+    double nu;          /* kinematic viscosity (lattice units) */
+    double rho0;        /* reference density; fields are stored as rho - rho0 */
+    int bc[6];          /* faces -x,+x,-y,+y,-z,+z: ACM_BC_*; a periodic face
+                           must be paired with a periodic face */
+    double lid_u[3];    /* wall velocity of ACM_BC_LID faces */
+    double g[3];        /* body force per unit mass: + dt rho^{n+1} g in Eq. (2.11) */
+    int two_phase;      /* 0 or 1: add phi, F_ST and the Cahn-Hilliard update */
+    double sigma;       /* surface tension */
+    double W;           /* interface width */
+    double M;           /* mobility */
+    int precision;      /* ACM_FP64 or ACM_FP32_DEV */
+    int sat_mask;       /* bit0: continuity SAT of Eq. (2.10), bit1: momentum
+                           SAT of Eq. (2.11); 3 = the paper's scheme, other
+                           values reproduce the ablation of Section 3.1 */
+} acm_params;
+
+/* Supported combinations (others return ACM_EINVAL):
+ *   dim 2: periodic, wall or lid faces; single- or two-phase (two-phase
+ *          requires periodic faces); FP64 or FP32_DEV;
+ *   dim 3: periodic faces, single-phase; FP64 or FP32_DEV.            */
+
+/* Create a solver for ONE grid.  Validates the parameters, allocates the
+ * double-buffered device fields on the current CUDA device and returns the
+ * handle in *out (NULL on failure).  The handle creates its own non-blocking
+ * CUDA stream (replace it with acm_set_stream).  Fields are undefined until
+ * acm_set_fields. */
+acm_status acm_create(const acm_params *params, acm_handle **out);
+
+/* Create a solver for NRUNS independent grids (a batch).  params[r] describes
+ * run r; all runs must share dim (2), precision, two_phase and the boundary
+ * kind.  Grid sizes and physical parameters may differ per run.  One
+ * acm_step advances every run by one step with one persistent kernel launch
+ * over a (run, tile) work list. */
+acm_status acm_batch_create(const acm_params *params, int nruns, acm_handle **out);
+
+/* Use this CUDA stream (a cudaStream_t, may be NULL for the legacy default
+ * stream) for every later call on the handle.  Invalidates captured graphs. */
+acm_status acm_set_stream(acm_handle *h, void *stream);
+
+/* Number of runs in the handle (1 for acm_create). */
+int acm_nruns(const acm_handle *h);
+
+/* Copy the initial state of run RUN from host memory: absolute density rho
+ * and velocity components (w ignored in 2D; phi required iff two_phase).
+ * Clears a sticky ACM_EUNSTABLE and resets the step counter of the handle.
+ * Synchronous. */
+acm_status acm_set_fields(acm_handle *h, int run, const double *rho, const double *u,
+                          const double *v, const double *w, const double *phi);
+
+/* Advance every run by NSTEPS time steps (asynchronous on the handle's
+ * stream; long runs are replayed from a captured CUDA graph). */
+acm_status acm_step(acm_handle *h, int64_t nsteps);
+
+/* Wait for the handle's stream and report a blow-up or a device timeout. */
+acm_status acm_sync(acm_handle *h);
+
+/* Copy the current state of run RUN to host memory (absolute density).
+ * Any pointer may be NULL.  Synchronous. */
+acm_status acm_fields(acm_handle *h, int run, double *rho, double *u, double *v, double *w,
+                      double *phi);
+
+/* FP64 integral diagnostics of every run (Section 3: kinetic energy of the
+ * Taylor-Green test, the steady-state criterion of the cavity test):
+ *   out[8*r + 0] = sum rho
+ *   out[8*r + 1..3] = sum rho u, sum rho v, sum rho w
+ *   out[8*r + 4] = E_k = 1/2 sum |u|^2
+ *   out[8*r + 5] = max over nodes of | |u^n| - |u^{n-1}| | (change made by
+ *                  the last step; 0 before the first step)
+ *   out[8*r + 6] = max |u|
+ *   out[8*r + 7] = number of non-finite values among rho and u
+ * OUT is a host array of 8 * acm_nruns(h) doubles.  Deterministic: the
+ * summation order does not depend on timing.  Synchronous. */
+acm_status acm_reduce_mass(acm_handle *h, double *out);
+
+/* Launch tuning knobs (the autotuner of the Python layer sweeps them).
+ * Changing a knob drops captured graphs.  Returns ACM_EINVAL for an unknown
+ * key or an out-of-range value. */
+enum {
+    ACM_TUNE_ZCHUNKS = 1,     /* 3D: z-chunks per x-y column (>= 1; 0 = heuristic) */
+    ACM_TUNE_T3Y = 2,         /* 3D: tile height in y, 8 or 16 */
+    ACM_TUNE_GRAPH_STEPS = 3, /* steps per captured CUDA graph, even, >= 2; 0 disables graphs */
+    ACM_TUNE_BLOCKS = 4       /* 2D: persistent CTAs per launch (0 = fill the GPU) */
+};
+acm_status acm_set_tuning(acm_handle *h, int key, int value);
+
+/* Step counter since acm_set_fields. */
+int64_t acm_step_count(const acm_handle *h);
+
+/* Free every resource of the handle (NULL is a no-op). */
+acm_status acm_destroy(acm_handle *h);
+
+/* Last error message of the handle, or of the calling thread when h is NULL
+ * (e.g. after a failed create).  Never NULL. */
+const char *acm_last_error(const acm_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ACM_H */

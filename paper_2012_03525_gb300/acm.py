@@ -1,0 +1,206 @@
+"""Thin ctypes binding of libacm (include/acm.h).  Argument marshalling only:
+every step of the solver runs in the library's CUDA kernels.  If the library
+has not been built, importing the binding raises -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libacm.so")
+
+OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5, -6
+BC_PERIODIC, BC_WALL, BC_LID = 0, 1, 2
+FP64, FP32_DEV = 0, 1
+TUNE_ZCHUNKS, TUNE_T3Y, TUNE_GRAPH_STEPS, TUNE_BLOCKS = 1, 2, 3, 4
+
+#: every symbol include/acm.h declares (checked by the CPU tests)
+EXPORTS = ["acm_create", "acm_batch_create", "acm_set_stream", "acm_nruns", "acm_set_fields",
+           "acm_step", "acm_sync", "acm_fields", "acm_reduce_mass", "acm_set_tuning",
+           "acm_step_count", "acm_destroy", "acm_last_error"]
+
+
+class AcmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"libacm status {status}: {msg}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("dt", ctypes.c_double), ("nu", ctypes.c_double), ("rho0", ctypes.c_double),
+        ("bc", ctypes.c_int * 6),
+        ("lid_u", ctypes.c_double * 3), ("g", ctypes.c_double * 3),
+        ("two_phase", ctypes.c_int),
+        ("sigma", ctypes.c_double), ("W", ctypes.c_double), ("M", ctypes.c_double),
+        ("precision", ctypes.c_int), ("sat_mask", ctypes.c_int),
+    ]
+
+
+_lib = None
+
+
+def load():
+    """Load libacm.so (built by ``paper_2012_03525_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: run paper_2012_03525_gb300.build.build() "
+                          "(there is no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    H = ctypes.c_void_p
+    P = ctypes.POINTER(Params)
+    dp = ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "acm_create": ([P, ctypes.POINTER(H)], ctypes.c_int),
+        "acm_batch_create": ([P, ctypes.c_int, ctypes.POINTER(H)], ctypes.c_int),
+        "acm_set_stream": ([H, ctypes.c_void_p], ctypes.c_int),
+        "acm_nruns": ([H], ctypes.c_int),
+        "acm_set_fields": ([H, ctypes.c_int, dp, dp, dp, dp, dp], ctypes.c_int),
+        "acm_step": ([H, ctypes.c_int64], ctypes.c_int),
+        "acm_sync": ([H], ctypes.c_int),
+        "acm_fields": ([H, ctypes.c_int, dp, dp, dp, dp, dp], ctypes.c_int),
+        "acm_reduce_mass": ([H, dp], ctypes.c_int),
+        "acm_set_tuning": ([H, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+        "acm_step_count": ([H], ctypes.c_int64),
+        "acm_destroy": ([H], ctypes.c_int),
+        "acm_last_error": ([H], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def make_params(shape, dt=1.0, nu=0.01, rho0=1.0, bc=None, lid_u=(0, 0, 0), g=(0, 0, 0),
+                two_phase=False, sigma=0.0, W=4.0, M=0.0, precision=FP64, sat_mask=3) -> Params:
+    """``shape`` is (ny, nx) for 2D or (nz, ny, nx) for 3D (array order)."""
+    p = Params()
+    if len(shape) == 2:
+        p.dim, p.nz, (p.ny, p.nx) = 2, 1, shape
+    else:
+        p.dim, (p.nz, p.ny, p.nx) = 3, shape
+    p.dt, p.nu, p.rho0 = dt, nu, rho0
+    bc = [BC_PERIODIC] * 6 if bc is None else list(bc)
+    for i in range(6):
+        p.bc[i] = bc[i]
+    for i in range(3):
+        p.lid_u[i] = lid_u[i]
+        p.g[i] = g[i]
+    p.two_phase = int(bool(two_phase))
+    p.sigma, p.W, p.M = sigma, W, M
+    p.precision = precision
+    p.sat_mask = sat_mask
+    return p
+
+
+def _dptr(a):
+    if a is None:
+        return None
+    if isinstance(a, int):  # raw (e.g. pinned) host address
+        return ctypes.cast(ctypes.c_void_p(a), ctypes.POINTER(ctypes.c_double))
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+class Solver:
+    """One handle: a single grid (``Solver(params)``) or a batch
+    (``Solver([params, ...])``)."""
+
+    def __init__(self, params):
+        lib = load()
+        self._lib = lib
+        self._h = ctypes.c_void_p()
+        if isinstance(params, (list, tuple)):
+            arr = (Params * len(params))(*params)
+            st = lib.acm_batch_create(arr, len(params), ctypes.byref(self._h))
+            self.params = list(params)
+        else:
+            st = lib.acm_create(ctypes.byref(params), ctypes.byref(self._h))
+            self.params = [params]
+        if st != OK:
+            raise AcmError(st, lib.acm_last_error(None).decode())
+
+    # -- helpers
+    def _check(self, st):
+        if st != OK:
+            raise AcmError(st, self._lib.acm_last_error(self._h).decode())
+        return st
+
+    def shape(self, run=0):
+        p = self.params[run]
+        return (p.ny, p.nx) if p.dim == 2 else (p.nz, p.ny, p.nx)
+
+    @property
+    def nruns(self):
+        return self._lib.acm_nruns(self._h)
+
+    # -- API
+    def set_stream(self, stream_ptr: int):
+        self._check(self._lib.acm_set_stream(self._h, ctypes.c_void_p(stream_ptr)))
+
+    def set_tuning(self, key: int, value: int):
+        self._check(self._lib.acm_set_tuning(self._h, key, value))
+
+    def set_fields(self, rho, u, v, w=None, phi=None, run=0):
+        self._check(self._lib.acm_set_fields(self._h, run, _dptr(rho), _dptr(u), _dptr(v),
+                                             _dptr(w), _dptr(phi)))
+
+    def step(self, n=1):
+        self._check(self._lib.acm_step(self._h, int(n)))
+
+    def sync(self):
+        return self._check(self._lib.acm_sync(self._h))
+
+    def fields(self, run=0, out=None):
+        """Returns (rho, u, v, w, phi) as float64 arrays (w/phi None when absent)."""
+        p = self.params[run]
+        shp = self.shape(run)
+        if out is None:
+            rho, u, v = np.empty(shp), np.empty(shp), np.empty(shp)
+            w = np.empty(shp) if p.dim == 3 else None
+            phi = np.empty(shp) if p.two_phase else None
+        else:
+            rho, u, v, w, phi = out
+        self._check(self._lib.acm_fields(self._h, run, _dptr(rho), _dptr(u), _dptr(v), _dptr(w),
+                                         _dptr(phi)))
+        return rho, u, v, w, phi
+
+    def fields_raw(self, run, ptrs):
+        """Copy into caller-provided host addresses (ints or None)."""
+        self._check(self._lib.acm_fields(self._h, run, *[_dptr(p) for p in ptrs]))
+
+    def set_fields_raw(self, run, ptrs):
+        self._check(self._lib.acm_set_fields(self._h, run, *[_dptr(p) for p in ptrs]))
+
+    def reduce(self):
+        out = np.zeros(8 * self.nruns)
+        self._check(self._lib.acm_reduce_mass(self._h, _dptr(out)))
+        return out.reshape(self.nruns, 8) if self.nruns > 1 else out
+
+    def step_count(self):
+        return self._lib.acm_step_count(self._h)
+
+    def close(self):
+        if self._h:
+            self._lib.acm_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

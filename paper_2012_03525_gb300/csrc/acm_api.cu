@@ -1,0 +1,619 @@
+// C ABI of libacm: handle life cycle, parameter validation, field transfer,
+// time stepping (with CUDA-graph replay) and diagnostics.  All arithmetic of
+// the scheme runs in the kernels of acm_step2d.cu / acm_step3d.cu /
+// acm_reduce.cu; this file only marshals.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "acm_internal.h"
+
+using namespace acm;
+
+struct acm_handle {
+    int nruns = 0, dim = 2, prec = ACM_FP64, two_phase = 0, any_wall = 0;
+    std::vector<acm_params> params;
+    std::vector<RunDesc> runs;
+    std::vector<long long> npoints;   // nodes per run
+    std::vector<char> have_fields;
+    RunDesc *druns = nullptr;
+    int4 *dwork = nullptr;
+    int nwork = 0;
+    size_t pool = 0;                  // elements per field pool
+    void *buf[2][NFIELD] = {};
+    int cur = 0;
+    int64_t steps = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    unsigned *derr = nullptr;
+    unsigned sticky = 0;
+    double *dpartials = nullptr;
+    int red_blocks = 0;
+    double *dout = nullptr;
+    double *dstage = nullptr;
+    CUtensorMap maps[2][4];
+    bool maps_ok = false;
+    cudaGraphExec_t gexec = nullptr;
+    Tuning tune;
+    std::string err;
+    int device = 0, sms = 0;
+    size_t esize() const { return prec == ACM_FP64 ? sizeof(double) : sizeof(float); }
+};
+
+namespace {
+
+thread_local std::string g_thread_err;
+
+acm_status fail(acm_handle *h, acm_status st, const std::string &msg)
+{
+    if (h) h->err = msg;
+    else g_thread_err = msg;
+    return st;
+}
+
+acm_status cuda_fail(acm_handle *h, cudaError_t e, const char *what)
+{
+    return fail(h, e == cudaErrorMemoryAllocation ? ACM_ENOMEM : ACM_ECUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(h, call)                                              \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return cuda_fail((h), e_, #call); \
+    } while (0)
+
+bool valid_bc(int b) { return b == ACM_BC_PERIODIC || b == ACM_BC_WALL || b == ACM_BC_LID; }
+
+acm_status validate(const acm_params &p, std::string &why)
+{
+    auto bad = [&](const char *m) {
+        why = m;
+        return ACM_EINVAL;
+    };
+    if (p.dim != 2 && p.dim != 3) return bad("dim must be 2 or 3");
+    if (p.nx < 1 || p.ny < 1 || (p.dim == 3 && p.nz < 1)) return bad("grid sizes must be >= 1");
+    if (p.dim == 2 && p.nz != 1) return bad("nz must be 1 in 2D");
+    if (!(p.dt > 0) || !std::isfinite(p.dt)) return bad("dt must be > 0");
+    if (!(p.nu >= 0) || !std::isfinite(p.nu)) return bad("nu must be >= 0");
+    if (!std::isfinite(p.rho0) || !(p.rho0 > 0)) return bad("rho0 must be > 0");
+    if (p.precision != ACM_FP64 && p.precision != ACM_FP32_DEV) return bad("bad precision");
+    if (p.sat_mask < 0 || p.sat_mask > 3) return bad("sat_mask must be 0..3");
+    const int n[3] = {p.nx, p.ny, p.nz};
+    for (int d = 0; d < 3; ++d) {
+        const int lo = p.bc[2 * d], hi = p.bc[2 * d + 1];
+        if (d >= p.dim) continue;
+        if (!valid_bc(lo) || !valid_bc(hi)) return bad("unknown boundary kind");
+        if ((lo == ACM_BC_PERIODIC) != (hi == ACM_BC_PERIODIC))
+            return bad("a periodic face must be paired with a periodic face");
+        if (lo != ACM_BC_PERIODIC && n[d] < 4) return bad("walls need >= 4 nodes across");
+    }
+    if (p.dim == 3) {
+        for (int f = 0; f < 6; ++f)
+            if (p.bc[f] != ACM_BC_PERIODIC) return bad("3D grids support periodic faces only");
+        if (p.nx < 2 || p.ny < 2) return bad("3D grids need nx, ny >= 2");
+        if (p.two_phase) return bad("two-phase runs are 2D only");
+    }
+    if (p.two_phase) {
+        for (int f = 0; f < 4; ++f)
+            if (p.bc[f] != ACM_BC_PERIODIC) return bad("two-phase runs need periodic faces");
+        if (!(p.W > 0) || !(p.sigma >= 0) || !(p.M >= 0)) return bad("bad sigma/W/M");
+    }
+    for (int d = 0; d < 3; ++d)
+        if (!std::isfinite(p.g[d]) || !std::isfinite(p.lid_u[d])) return bad("non-finite g/lid");
+    return ACM_OK;
+}
+
+RunDesc describe(const acm_params &p)
+{
+    RunDesc r;
+    std::memset(&r, 0, sizeof(r));
+    r.nx = p.nx;
+    r.ny = p.ny;
+    r.nz = p.dim == 3 ? p.nz : 1;
+    for (int f = 0; f < 6; ++f) r.bc[f] = p.bc[f];
+    r.rho0 = p.rho0;
+    r.dt = p.dt;
+    r.cs2 = 1.0 / (3.0 * p.dt * p.dt);
+    r.nu = p.nu;
+    for (int d = 0; d < 3; ++d) {
+        r.g[d] = p.g[d];
+        r.lid[d] = p.lid_u[d];
+    }
+    r.two_phase = p.two_phase;
+    r.a = 3.0 * p.sigma / (4.0 * p.W);
+    r.kappa = 3.0 * p.sigma * p.W / 8.0;
+    r.M = p.M;
+    r.sat_c = p.sat_mask & 1;
+    r.sat_m = (p.sat_mask >> 1) & 1;
+    double c[NCOEF];
+    c[C_RHO0] = r.rho0;
+    c[C_DT] = r.dt;
+    c[C_CS2] = r.cs2;
+    c[C_NU] = r.nu;
+    c[C_SATC] = r.sat_c ? 0.5 * r.cs2 * r.dt * r.dt : 0.0;
+    c[C_SATM] = r.sat_m ? r.nu + 0.5 * r.cs2 * r.dt : 0.0;
+    c[C_NUDT] = r.nu * r.dt;
+    c[C_GX] = r.g[0];
+    c[C_GY] = r.g[1];
+    c[C_GZ] = r.g[2];
+    c[C_LIDX] = r.lid[0];
+    c[C_LIDY] = r.lid[1];
+    c[C_LIDZ] = r.lid[2];
+    c[C_A] = r.a;
+    c[C_KAPPA] = r.kappa;
+    c[C_M] = r.M;
+    for (int k = 0; k < NCOEF; ++k) {
+        r.cd[k] = c[k];
+        r.cf[k] = (float)c[k];
+    }
+    if (p.dim == 3) {
+        r.pad = T3PAD;
+        r.px = ((p.nx + 2 * T3PAD + 7) / 8) * 8;
+        r.py = p.ny + 2 * T3PAD;
+    } else {
+        r.pad = 0;
+        r.px = p.nx;
+        r.py = p.ny;
+    }
+    return r;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+acm_status build_maps(acm_handle *h)
+{
+    h->maps_ok = false;
+    if (h->dim != 3) return ACM_OK;
+    auto fn = encode_fn();
+    if (!fn) return fail(h, ACM_ECUDA, "cuTensorMapEncodeTiled is not available");
+    const RunDesc &R = h->runs[0];
+    const size_t es = h->esize();
+    cuuint64_t dims[3] = {(cuuint64_t)R.px, (cuuint64_t)R.py, (cuuint64_t)R.nz};
+    cuuint64_t strides[2] = {(cuuint64_t)(R.px * es), (cuuint64_t)(R.px * R.py * es)};
+    cuuint32_t box[3] = {(cuuint32_t)(T3X + 4), (cuuint32_t)(h->tune.t3y + 4), 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    const CUtensorMapDataType dt =
+        h->prec == ACM_FP64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    for (int b = 0; b < 2; ++b)
+        for (int f = 0; f < 4; ++f) {
+            CUresult r = fn(&h->maps[b][f], dt, 3, h->buf[b][f], dims, strides, box, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS)
+                return fail(h, ACM_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string(r) + ")");
+        }
+    h->maps_ok = true;
+    return ACM_OK;
+}
+
+void drop_graph(acm_handle *h)
+{
+    if (h->gexec) {
+        cudaGraphExecDestroy(h->gexec);
+        h->gexec = nullptr;
+    }
+}
+
+void release(acm_handle *h)
+{
+    drop_graph(h);
+    for (int b = 0; b < 2; ++b)
+        for (int f = 0; f < NFIELD; ++f)
+            if (h->buf[b][f]) cudaFree(h->buf[b][f]);
+    if (h->druns) cudaFree(h->druns);
+    if (h->dwork) cudaFree(h->dwork);
+    if (h->derr) cudaFree(h->derr);
+    if (h->dpartials) cudaFree(h->dpartials);
+    if (h->dout) cudaFree(h->dout);
+    if (h->dstage) cudaFree(h->dstage);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+}
+
+bool field_used(const acm_handle *h, int f)
+{
+    if (f == F_W) return h->dim == 3;
+    if (f == F_PHI) return h->two_phase != 0;
+    return true;
+}
+
+acm_status create_common(const acm_params *params, int nruns, acm_handle **out)
+{
+    if (out) *out = nullptr;
+    if (!params || !out || nruns < 1) return fail(nullptr, ACM_EINVAL, "null argument or nruns < 1");
+    std::string why;
+    for (int r = 0; r < nruns; ++r)
+        if (validate(params[r], why) != ACM_OK)
+            return fail(nullptr, ACM_EINVAL, "run " + std::to_string(r) + ": " + why);
+    const acm_params &p0 = params[0];
+    if (nruns > 1) {
+        if (p0.dim != 2) return fail(nullptr, ACM_EINVAL, "batches are 2D only");
+        for (int r = 1; r < nruns; ++r) {
+            const acm_params &p = params[r];
+            if (p.dim != p0.dim || p.precision != p0.precision || p.two_phase != p0.two_phase)
+                return fail(nullptr, ACM_EINVAL, "batch runs must share dim, precision, two_phase");
+        }
+    }
+    acm_handle *h = new (std::nothrow) acm_handle();
+    if (!h) return fail(nullptr, ACM_ENOMEM, "host allocation failed");
+    h->nruns = nruns;
+    h->dim = p0.dim;
+    h->prec = p0.precision;
+    h->two_phase = p0.two_phase;
+    h->params.assign(params, params + nruns);
+    h->have_fields.assign(nruns, 0);
+    auto bail = [&](acm_status st) {
+        std::string m = h->err;
+        release(h);
+        delete h;
+        return fail(nullptr, st, m);
+    };
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) {
+        cuda_fail(h, e, "cudaGetDevice");
+        return bail(ACM_ECUDA);
+    }
+    cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (h->sms <= 0) h->sms = 1;
+
+    // per-run descriptors, pool offsets (each run starts on a 256-byte boundary)
+    size_t off = 0;
+    long long maxn = 0;
+    std::vector<int4> work;
+    for (int r = 0; r < nruns; ++r) {
+        RunDesc d = describe(params[r]);
+        d.off = (long long)off;
+        const size_t n = (size_t)d.px * d.py * d.nz;
+        off += (n + 31) / 32 * 32;
+        h->runs.push_back(d);
+        const long long np = (long long)d.nx * d.ny * d.nz;
+        h->npoints.push_back(np);
+        maxn = std::max(maxn, np);
+        for (int f = 0; f < 4; ++f)
+            if (d.bc[f] != ACM_BC_PERIODIC) h->any_wall = 1;
+        if (h->dim == 2) {
+            const int tx = (d.nx + T2X - 1) / T2X, ty = (d.ny + T2Y - 1) / T2Y;
+            for (int j = 0; j < ty; ++j)
+                for (int i = 0; i < tx; ++i) {
+                    const int x0 = std::min(i * T2X, std::max(d.nx - T2X, 0));
+                    const int y0 = std::min(j * T2Y, std::max(d.ny - T2Y, 0));
+                    work.push_back(make_int4(r, x0, y0, 0));
+                }
+        }
+    }
+    h->pool = off;
+    h->nwork = (int)work.size();
+
+#define CKB(call)                                    \
+    do {                                             \
+        cudaError_t e_ = (call);                     \
+        if (e_ != cudaSuccess) {                     \
+            acm_status st_ = cuda_fail(h, e_, #call); \
+            return bail(st_);                        \
+        }                                            \
+    } while (0)
+
+    CKB(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+    h->own_stream = true;
+    for (int b = 0; b < 2; ++b)
+        for (int f = 0; f < NFIELD; ++f)
+            if (field_used(h, f)) {
+                CKB(cudaMalloc(&h->buf[b][f], h->pool * h->esize()));
+                CKB(cudaMemset(h->buf[b][f], 0, h->pool * h->esize()));
+            }
+    CKB(cudaMalloc(&h->druns, sizeof(RunDesc) * nruns));
+    CKB(cudaMemcpy(h->druns, h->runs.data(), sizeof(RunDesc) * nruns, cudaMemcpyHostToDevice));
+    if (!work.empty()) {
+        CKB(cudaMalloc(&h->dwork, sizeof(int4) * work.size()));
+        CKB(cudaMemcpy(h->dwork, work.data(), sizeof(int4) * work.size(), cudaMemcpyHostToDevice));
+    }
+    CKB(cudaMalloc(&h->derr, sizeof(unsigned)));
+    CKB(cudaMemset(h->derr, 0, sizeof(unsigned)));
+    const long long per_run_blocks = (maxn + 255) / 256;
+    h->red_blocks = (int)std::max<long long>(
+        1, std::min<long long>(per_run_blocks, nruns == 1 ? 4LL * h->sms : 16LL));
+    CKB(cudaMalloc(&h->dpartials, sizeof(double) * 8 * (size_t)h->red_blocks * nruns));
+    CKB(cudaMalloc(&h->dout, sizeof(double) * 8 * nruns));
+    CKB(cudaMalloc(&h->dstage, sizeof(double) * (size_t)maxn));
+    if (build_maps(h) != ACM_OK) return bail(ACM_ECUDA);
+    // resolve launch attributes now, not inside a later stream capture
+    if (h->dim == 2) {
+        if (h->prec == ACM_FP64) step2d_max_blocks_per_sm<double>(h->two_phase);
+        else step2d_max_blocks_per_sm<float>(h->two_phase);
+    } else {
+        for (int t3y : {8, 16}) {
+            if (h->prec == ACM_FP64) step3d_max_blocks_per_sm<double>(t3y);
+            else step3d_max_blocks_per_sm<float>(t3y);
+        }
+    }
+    *out = h;
+    return ACM_OK;
+}
+
+template <typename T>
+Fields<T> fields_of(acm_handle *h, int b)
+{
+    Fields<T> f;
+    for (int k = 0; k < NFIELD; ++k) f.f[k] = static_cast<T *>(h->buf[b][k]);
+    return f;
+}
+
+template <typename T>
+cudaError_t one_step(acm_handle *h, int from)
+{
+    Fields<T> in = fields_of<T>(h, from), out = fields_of<T>(h, 1 - from);
+    if (h->dim == 3) {
+        const RunDesc &R = h->runs[0];
+        int zc = h->tune.zchunks;
+        if (zc <= 0) {
+            // fill the GPU with about one wave of CTAs
+            const long long cols = (long long)((R.nx + T3X - 1) / T3X) *
+                                   ((R.ny + h->tune.t3y - 1) / h->tune.t3y);
+            const long long slots = (long long)h->sms * step3d_max_blocks_per_sm<T>(h->tune.t3y);
+            zc = (int)std::max<long long>(1, std::min<long long>(R.nz, (slots + cols - 1) / cols));
+        }
+        return launch_step3d<T>(h->maps[from], out, R, h->derr, zc, h->tune.t3y, h->stream);
+    }
+    int blocks = h->tune.blocks;
+    if (blocks <= 0) blocks = h->sms * step2d_max_blocks_per_sm<T>(h->two_phase);
+    return launch_step2d<T>(h->druns, h->dwork, h->nwork, h->two_phase, in, out, h->derr, blocks,
+                            h->stream);
+}
+
+cudaError_t step_once(acm_handle *h, int from)
+{
+    return h->prec == ACM_FP64 ? one_step<double>(h, from) : one_step<float>(h, from);
+}
+
+acm_status ensure_graph(acm_handle *h)
+{
+    if (h->gexec) return ACM_OK;
+    cudaGraph_t g = nullptr;
+    CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t le = cudaSuccess;
+    for (int k = 0; k < h->tune.graph_steps && le == cudaSuccess; ++k) le = step_once(h, k & 1);
+    cudaError_t ee = cudaStreamEndCapture(h->stream, &g);
+    if (le != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(h, le, "kernel launch during capture");
+    }
+    if (ee != cudaSuccess) return cuda_fail(h, ee, "cudaStreamEndCapture");
+    cudaError_t ie = cudaGraphInstantiate(&h->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) {
+        h->gexec = nullptr;
+        return cuda_fail(h, ie, "cudaGraphInstantiate");
+    }
+    return ACM_OK;
+}
+
+acm_status check_flags(acm_handle *h)
+{
+    unsigned flags = 0;
+    CK(h, cudaMemcpyAsync(&flags, h->derr, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    h->sticky |= flags;
+    if (h->sticky & ERR_TIMEOUT) return fail(h, ACM_ETIMEOUT, "a device-side wait timed out");
+    if (h->sticky & ERR_NONFINITE)
+        return fail(h, ACM_EUNSTABLE, "non-finite values in the fields (numerical blow-up)");
+    return ACM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+acm_status acm_create(const acm_params *params, acm_handle **out)
+{
+    return create_common(params, 1, out);
+}
+
+acm_status acm_batch_create(const acm_params *params, int nruns, acm_handle **out)
+{
+    return create_common(params, nruns, out);
+}
+
+acm_status acm_set_stream(acm_handle *h, void *stream)
+{
+    if (!h) return fail(nullptr, ACM_EINVAL, "null handle");
+    drop_graph(h);
+    if (h->own_stream && h->stream) {
+        cudaStreamSynchronize(h->stream);
+        cudaStreamDestroy(h->stream);
+    }
+    h->own_stream = false;
+    h->stream = static_cast<cudaStream_t>(stream);
+    return ACM_OK;
+}
+
+int acm_nruns(const acm_handle *h) { return h ? h->nruns : 0; }
+
+int64_t acm_step_count(const acm_handle *h) { return h ? h->steps : -1; }
+
+acm_status acm_set_tuning(acm_handle *h, int key, int value)
+{
+    if (!h) return fail(nullptr, ACM_EINVAL, "null handle");
+    switch (key) {
+    case ACM_TUNE_ZCHUNKS:
+        if (value < 0) return fail(h, ACM_EINVAL, "zchunks must be >= 0");
+        h->tune.zchunks = value;
+        break;
+    case ACM_TUNE_T3Y:
+        if (value != 8 && value != 16) return fail(h, ACM_EINVAL, "t3y must be 8 or 16");
+        if (value != h->tune.t3y) {
+            cudaSetDevice(h->device);
+            CK(h, cudaStreamSynchronize(h->stream));
+            h->tune.t3y = value;
+            if (build_maps(h) != ACM_OK) return ACM_ECUDA;
+        }
+        break;
+    case ACM_TUNE_GRAPH_STEPS:
+        if (value < 0 || (value & 1)) return fail(h, ACM_EINVAL, "graph_steps must be even >= 0");
+        h->tune.graph_steps = value;
+        break;
+    case ACM_TUNE_BLOCKS:
+        if (value < 0) return fail(h, ACM_EINVAL, "blocks must be >= 0");
+        h->tune.blocks = value;
+        break;
+    default:
+        return fail(h, ACM_EINVAL, "unknown tuning key");
+    }
+    drop_graph(h);
+    return ACM_OK;
+}
+
+acm_status acm_set_fields(acm_handle *h, int run, const double *rho, const double *u,
+                          const double *v, const double *w, const double *phi)
+{
+    if (!h) return fail(nullptr, ACM_EINVAL, "null handle");
+    if (run < 0 || run >= h->nruns) return fail(h, ACM_EINVAL, "run index out of range");
+    if (!rho || !u || !v || (h->dim == 3 && !w) || (h->two_phase && !phi))
+        return fail(h, ACM_EINVAL, "missing field");
+    CK(h, cudaSetDevice(h->device));
+    const RunDesc &R = h->runs[run];
+    const size_t n = (size_t)h->npoints[run];
+    const double *src[NFIELD] = {rho, u, v, w, phi};
+    for (int f = 0; f < NFIELD; ++f) {
+        if (!field_used(h, f)) continue;
+        const double shift = f == F_R ? R.rho0 : 0.0;
+        CK(h, cudaMemcpyAsync(h->dstage, src[f], n * sizeof(double), cudaMemcpyHostToDevice,
+                              h->stream));
+        cudaError_t e = h->prec == ACM_FP64
+                            ? launch_import<double>(h->dstage,
+                                                    static_cast<double *>(h->buf[h->cur][f]), R,
+                                                    h->dim, shift, h->stream)
+                            : launch_import<float>(h->dstage, static_cast<float *>(h->buf[h->cur][f]),
+                                                   R, h->dim, shift, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "import kernel");
+    }
+    CK(h, cudaMemsetAsync(h->derr, 0, sizeof(unsigned), h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    h->sticky = 0;
+    h->steps = 0;
+    h->have_fields[run] = 1;
+    return ACM_OK;
+}
+
+acm_status acm_step(acm_handle *h, int64_t nsteps)
+{
+    if (!h) return fail(nullptr, ACM_EINVAL, "null handle");
+    if (nsteps < 0) return fail(h, ACM_EINVAL, "nsteps must be >= 0");
+    for (int r = 0; r < h->nruns; ++r)
+        if (!h->have_fields[r]) return fail(h, ACM_ESTATE, "acm_set_fields not called for every run");
+    if (h->sticky & ERR_TIMEOUT) return fail(h, ACM_ETIMEOUT, "a device-side wait timed out");
+    if (h->sticky & ERR_NONFINITE) return fail(h, ACM_EUNSTABLE, "fields already non-finite");
+    CK(h, cudaSetDevice(h->device));
+    int64_t left = nsteps;
+    const int G = h->tune.graph_steps;
+    if (h->cur == 1 && left > 0) {
+        CK(h, step_once(h, 1));
+        h->cur = 0;
+        --left;
+    }
+    if (G > 0 && h->stream != nullptr && left >= G) {
+        acm_status st = ensure_graph(h);
+        if (st != ACM_OK) return st;
+        while (left >= G) {
+            CK(h, cudaGraphLaunch(h->gexec, h->stream));
+            left -= G;
+        }
+    }
+    while (left > 0) {
+        CK(h, step_once(h, h->cur));
+        h->cur ^= 1;
+        --left;
+    }
+    h->steps += nsteps;
+    return ACM_OK;
+}
+
+acm_status acm_sync(acm_handle *h)
+{
+    if (!h) return fail(nullptr, ACM_EINVAL, "null handle");
+    CK(h, cudaSetDevice(h->device));
+    return check_flags(h);
+}
+
+acm_status acm_fields(acm_handle *h, int run, double *rho, double *u, double *v, double *w,
+                      double *phi)
+{
+    if (!h) return fail(nullptr, ACM_EINVAL, "null handle");
+    if (run < 0 || run >= h->nruns) return fail(h, ACM_EINVAL, "run index out of range");
+    CK(h, cudaSetDevice(h->device));
+    const RunDesc &R = h->runs[run];
+    const size_t n = (size_t)h->npoints[run];
+    double *dst[NFIELD] = {rho, u, v, w, phi};
+    for (int f = 0; f < NFIELD; ++f) {
+        if (!dst[f] || !field_used(h, f)) continue;
+        const double shift = f == F_R ? R.rho0 : 0.0;
+        cudaError_t e =
+            h->prec == ACM_FP64
+                ? launch_export<double>(static_cast<const double *>(h->buf[h->cur][f]), h->dstage,
+                                        R, h->dim, shift, h->stream)
+                : launch_export<float>(static_cast<const float *>(h->buf[h->cur][f]), h->dstage, R,
+                                       h->dim, shift, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "export kernel");
+        CK(h, cudaMemcpyAsync(dst[f], h->dstage, n * sizeof(double), cudaMemcpyDeviceToHost,
+                              h->stream));
+    }
+    return check_flags(h);
+}
+
+acm_status acm_reduce_mass(acm_handle *h, double *out)
+{
+    if (!h || !out) return fail(h, ACM_EINVAL, "null argument");
+    CK(h, cudaSetDevice(h->device));
+    const int prev = 1 - h->cur;
+    const bool have_prev = h->steps > 0;
+    cudaError_t e;
+    if (h->prec == ACM_FP64) {
+        const double *pu = have_prev ? static_cast<const double *>(h->buf[prev][F_U]) : nullptr;
+        const double *pv = have_prev ? static_cast<const double *>(h->buf[prev][F_V]) : nullptr;
+        const double *pw = have_prev ? static_cast<const double *>(h->buf[prev][F_W]) : nullptr;
+        e = launch_reduce<double>(h->druns, h->nruns, h->dim, fields_of<double>(h, h->cur), pu, pv,
+                                  pw, h->dpartials, h->red_blocks, h->dout, h->stream);
+    } else {
+        const float *pu = have_prev ? static_cast<const float *>(h->buf[prev][F_U]) : nullptr;
+        const float *pv = have_prev ? static_cast<const float *>(h->buf[prev][F_V]) : nullptr;
+        const float *pw = have_prev ? static_cast<const float *>(h->buf[prev][F_W]) : nullptr;
+        e = launch_reduce<float>(h->druns, h->nruns, h->dim, fields_of<float>(h, h->cur), pu, pv,
+                                 pw, h->dpartials, h->red_blocks, h->dout, h->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "reduction kernels");
+    CK(h, cudaMemcpyAsync(out, h->dout, sizeof(double) * 8 * h->nruns, cudaMemcpyDeviceToHost,
+                          h->stream));
+    return check_flags(h);
+}
+
+acm_status acm_destroy(acm_handle *h)
+{
+    if (!h) return ACM_OK;
+    cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    release(h);
+    delete h;
+    return ACM_OK;
+}
+
+const char *acm_last_error(const acm_handle *h)
+{
+    return h ? h->err.c_str() : g_thread_err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,111 @@
+// Internal declarations shared by the libacm translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/acm.h"
+
+namespace acm {
+
+// Field slots in every buffer (structure of arrays).
+enum { F_R = 0, F_U = 1, F_V = 2, F_W = 3, F_PHI = 4, NFIELD = 5 };
+
+// Device error word bits.
+enum : unsigned { ERR_NONFINITE = 1u, ERR_TIMEOUT = 2u };
+
+template <typename T>
+struct Fields {
+    T *f[NFIELD];
+};
+
+// Per-run coefficients, stored in both precisions so that kernels never
+// convert (a double->float conversion runs on the FP64 pipe, which is narrow
+// on GB300).
+enum {
+    C_RHO0 = 0, C_DT, C_CS2, C_NU,
+    C_SATC,   // 1/2 c_s^2 dt^2 if the continuity SAT is on, else 0 (Eq. 2.10)
+    C_SATM,   // nu + 1/2 c_s^2 dt if the momentum SAT is on, else 0 (Eq. 2.11)
+    C_NUDT,   // nu dt
+    C_GX, C_GY, C_GZ, C_LIDX, C_LIDY, C_LIDZ,
+    C_A, C_KAPPA, C_M,
+    NCOEF
+};
+
+// Per-run description used by the 2D tile kernels and the reductions.
+struct RunDesc {
+    int nx, ny, nz;
+    int bc[6];          // ACM_BC_* per face
+    long long off;      // element offset of the run inside each field pool
+    long long px, py;   // storage pitch (elements) in x and y (3D: padded)
+    int pad;            // ghost layers in x and y (3D TMA layout), 0 in 2D
+    double rho0, dt, cs2, nu;
+    double g[3], lid[3];
+    double a, kappa, M; // two-phase coefficients
+    int sat_c, sat_m;
+    int two_phase;
+    float cf[NCOEF];
+    double cd[NCOEF];
+};
+
+template <typename T>
+__host__ __device__ __forceinline__ const T *coefs(const RunDesc &R);
+template <>
+__host__ __device__ __forceinline__ const float *coefs<float>(const RunDesc &R)
+{
+    return R.cf;
+}
+template <>
+__host__ __device__ __forceinline__ const double *coefs<double>(const RunDesc &R)
+{
+    return R.cd;
+}
+
+// 2D tile geometry (outputs per tile).
+constexpr int T2X = 32;
+constexpr int T2Y = 16;
+constexpr int T2THREADS = 256;
+
+// 3D z-marching kernel geometry.
+constexpr int T3X = 32;
+constexpr int T3PAD = 2;     // ghost layers in x and y of the 3D layout
+constexpr int T3SLOTS = 5;   // input planes resident/in flight per CTA
+
+struct Tuning {
+    int zchunks = 0;       // 3D: z-chunks per column (0 = heuristic)
+    int t3y = 8;           // 3D: tile height (8 or 16)
+    int graph_steps = 64;  // steps per captured CUDA graph (even)
+    int blocks = 0;        // 2D: persistent CTAs (0 = occupancy x SMs)
+};
+
+// Launchers (defined in the kernel translation units).
+template <typename T>
+cudaError_t launch_step2d(const RunDesc *druns, const int4 *dwork, int nwork, int two_phase,
+                          Fields<T> in, Fields<T> out, unsigned *derr, int blocks,
+                          cudaStream_t s);
+template <typename T>
+int step2d_max_blocks_per_sm(int two_phase);
+
+template <typename T>
+cudaError_t launch_step3d(const CUtensorMap *maps_in, Fields<T> out, const RunDesc &run,
+                          unsigned *derr, int zchunks, int t3y, cudaStream_t s);
+template <typename T>
+int step3d_max_blocks_per_sm(int t3y);
+
+template <typename T>
+cudaError_t launch_reduce(const RunDesc *druns, int nruns, int dim, Fields<T> cur, const T *pu,
+                          const T *pv, const T *pw, double *dpartials, int blocks_per_run,
+                          double *dout, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_import(const double *src, T *dst, const RunDesc &run, int dim, double shift,
+                          cudaStream_t s);
+template <typename T>
+cudaError_t launch_export(const T *src, double *dst, const RunDesc &run, int dim, double shift,
+                          cudaStream_t s);
+
+}  // namespace acm

@@ -1,0 +1,179 @@
+// FP64 integral diagnostics and host<->storage conversion kernels.
+//
+// Diagnostics (Section 3 of Huang, arXiv:2012.03525: kinetic energy of the
+// Taylor-Green test, the steady-state criterion max |  |u|^{n+1} - |u|^n  |
+// of the cavity test) are accumulated in FP64 for both storage precisions.
+// Deterministic two-pass reduction: pass 1 gives every (run, block) a fixed
+// strided slice of the nodes and reduces it in a fixed tree; pass 2 sums the
+// block partials of each run in block order.  The result does not depend on
+// scheduling.
+#include "acm_internal.h"
+
+namespace acm {
+namespace {
+
+constexpr int RT = 256;  // reduction threads per block
+
+__device__ __forceinline__ long long storage_index(const RunDesc &R, int dim, long long i)
+{
+    if (dim == 2) return R.off + i;
+    const long long nxy = (long long)R.nx * R.ny;
+    const long long z = i / nxy;
+    const long long rem = i - z * nxy;
+    const long long y = rem / R.nx;
+    const long long x = rem - y * R.nx;
+    return R.off + (z * R.py + y + R.pad) * R.px + x + R.pad;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(RT)
+    k_reduce(const RunDesc *__restrict__ runs, int dim, Fields<T> cur, const T *pu, const T *pv,
+             const T *pw, double *partials)
+{
+    const RunDesc &R = runs[blockIdx.y];
+    const long long n = (long long)R.nx * R.ny * R.nz;
+    double s[5] = {0, 0, 0, 0, 0};
+    double mdu = 0.0, mu = 0.0, nbad = 0.0;
+    const double rho0 = R.rho0;
+    for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < n;
+         i += (long long)gridDim.x * RT) {
+        const long long k = storage_index(R, dim, i);
+        const double r = (double)cur.f[F_R][k];
+        const double u = (double)cur.f[F_U][k];
+        const double v = (double)cur.f[F_V][k];
+        const double w = dim == 3 ? (double)cur.f[F_W][k] : 0.0;
+        const double rho = rho0 + r;
+        s[0] += r;
+        s[1] += rho * u;
+        s[2] += rho * v;
+        s[3] += rho * w;
+        const double q = u * u + v * v + w * w;
+        s[4] += 0.5 * q;
+        const double sp = sqrt(q);
+        mu = fmax(mu, sp);
+        if (pu) {
+            const double a = (double)pu[k], b = (double)pv[k], c = dim == 3 ? (double)pw[k] : 0.0;
+            mdu = fmax(mdu, fabs(sp - sqrt(a * a + b * b + c * c)));
+        }
+        nbad += (!isfinite(r) || !isfinite(u) || !isfinite(v) || !isfinite(w)) ? 1.0 : 0.0;
+    }
+    double vals[8] = {s[0], s[1], s[2], s[3], s[4], mdu, mu, nbad};
+    __shared__ double red[8][RT / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        double x = vals[q];
+        for (int o = 16; o > 0; o >>= 1) {
+            const double y = __shfl_down_sync(0xffffffffu, x, o);
+            x = (q == 5 || q == 6) ? fmax(x, y) : x + y;
+        }
+        if (lane == 0) red[q][wid] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        const int q = threadIdx.x;
+        double x = red[q][0];
+        for (int k = 1; k < RT / 32; ++k) x = (q == 5 || q == 6) ? fmax(x, red[q][k]) : x + red[q][k];
+        partials[((long long)blockIdx.y * gridDim.x + blockIdx.x) * 8 + q] = x;
+    }
+}
+
+__global__ void k_reduce_final(const RunDesc *__restrict__ runs, const double *partials,
+                               int blocks_per_run, double *out)
+{
+    const int r = blockIdx.x;
+    const int q = threadIdx.x;
+    if (q >= 8) return;
+    double x = partials[(long long)r * blocks_per_run * 8 + q];
+    for (int b = 1; b < blocks_per_run; ++b) {
+        const double y = partials[((long long)r * blocks_per_run + b) * 8 + q];
+        x = (q == 5 || q == 6) ? fmax(x, y) : x + y;
+    }
+    if (q == 0) {
+        const RunDesc &R = runs[r];
+        x += (double)R.nx * R.ny * R.nz * R.rho0;
+    }
+    out[r * 8 + q] = x;
+}
+
+// host FP64 staging (unpadded, [z][y][x]) -> storage (shifted, padded in 3D,
+// ghost layers filled with the periodic images)
+template <typename T>
+__global__ void k_import(const double *__restrict__ src, T *__restrict__ dst, RunDesc R, int dim,
+                         double shift)
+{
+    if (dim == 2) {
+        const long long n = (long long)R.nx * R.ny;
+        for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+             i += (long long)gridDim.x * blockDim.x)
+            dst[R.off + i] = (T)(src[i] - shift);
+        return;
+    }
+    const long long n = R.px * R.py * R.nz;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long z = i / (R.px * R.py);
+        const long long rem = i - z * R.px * R.py;
+        long long y = rem / R.px - R.pad;
+        long long x = rem % R.px - R.pad;
+        y = ((y % R.ny) + R.ny) % R.ny;
+        x = ((x % R.nx) + R.nx) % R.nx;
+        dst[R.off + i] = (T)(src[(z * R.ny + y) * R.nx + x] - shift);
+    }
+}
+
+template <typename T>
+__global__ void k_export(const T *__restrict__ src, double *__restrict__ dst, RunDesc R, int dim,
+                         double shift)
+{
+    const long long n = (long long)R.nx * R.ny * R.nz;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        dst[i] = (double)src[storage_index(R, dim, i)] + shift;
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_reduce(const RunDesc *druns, int nruns, int dim, Fields<T> cur, const T *pu,
+                          const T *pv, const T *pw, double *dpartials, int blocks_per_run,
+                          double *dout, cudaStream_t s)
+{
+    dim3 grid(blocks_per_run, nruns);
+    k_reduce<T><<<grid, RT, 0, s>>>(druns, dim, cur, pu, pv, pw, dpartials);
+    k_reduce_final<<<nruns, 32, 0, s>>>(druns, dpartials, blocks_per_run, dout);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_import(const double *src, T *dst, const RunDesc &run, int dim, double shift,
+                          cudaStream_t s)
+{
+    k_import<T><<<1024, 256, 0, s>>>(src, dst, run, dim, shift);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_export(const T *src, double *dst, const RunDesc &run, int dim, double shift,
+                          cudaStream_t s)
+{
+    k_export<T><<<1024, 256, 0, s>>>(src, dst, run, dim, shift);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_reduce<float>(const RunDesc *, int, int, Fields<float>, const float *,
+                                          const float *, const float *, double *, int, double *,
+                                          cudaStream_t);
+template cudaError_t launch_reduce<double>(const RunDesc *, int, int, Fields<double>,
+                                           const double *, const double *, const double *,
+                                           double *, int, double *, cudaStream_t);
+template cudaError_t launch_import<float>(const double *, float *, const RunDesc &, int, double,
+                                          cudaStream_t);
+template cudaError_t launch_import<double>(const double *, double *, const RunDesc &, int, double,
+                                           cudaStream_t);
+template cudaError_t launch_export<float>(const float *, double *, const RunDesc &, int, double,
+                                          cudaStream_t);
+template cudaError_t launch_export<double>(const double *, double *, const RunDesc &, int, double,
+                                           cudaStream_t);
+
+}  // namespace acm

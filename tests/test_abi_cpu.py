@@ -1,0 +1,83 @@
+"""CPU-side checks of the C ABI: the library loads, exports every symbol that
+include/acm.h declares, and rejects invalid parameters before touching a GPU.
+No compute call is made here."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2012_03525_gb300 import acm, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return acm.load()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "acm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(acm_[a-z_]+)\s*\(", src)))
+
+
+def test_header_and_binding_agree():
+    assert declared_functions() == sorted(acm.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_params_struct_layout_matches_header():
+    # field order/types of acm_params as declared in include/acm.h
+    src = open(os.path.join(ROOT, "include", "acm.h")).read()
+    body = src[src.index("typedef struct {"):src.index("} acm_params;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    names = re.findall(r"(?:int|double)\s+([^;]+);", body)
+    flat = []
+    for group in names:
+        for n in group.split(","):
+            flat.append(re.sub(r"\[.*\]", "", n).strip())
+    assert flat == [f[0] for f in acm.Params._fields_]
+
+
+@pytest.mark.parametrize("kw,msg", [
+    (dict(shape=(8, 8), dt=0.0), "dt"),
+    (dict(shape=(8, 8), nu=-1.0), "nu"),
+    (dict(shape=(8, 8), bc=[1, 0, 0, 0, 0, 0]), "periodic"),
+    (dict(shape=(3, 8), bc=[0, 0, 1, 1, 0, 0]), "walls"),
+    (dict(shape=(4, 8, 8), bc=[1, 1, 0, 0, 0, 0]), "3D"),
+    (dict(shape=(8, 8), two_phase=True, W=0.0), "sigma/W/M"),
+    (dict(shape=(8, 8), two_phase=True, bc=[1, 1, 0, 0, 0, 0]), "two-phase"),
+    (dict(shape=(8, 8), sat_mask=4), "sat_mask"),
+    (dict(shape=(8, 8), precision=7), "precision"),
+])
+def test_invalid_params_rejected_on_host(lib, kw, msg):
+    shape = kw.pop("shape")
+    p = acm.make_params(shape, **kw)
+    h = ctypes.c_void_p()
+    st = lib.acm_create(ctypes.byref(p), ctypes.byref(h))
+    assert st == acm.EINVAL
+    assert not h.value
+    assert msg in lib.acm_last_error(None).decode()
+
+
+def test_batch_must_share_precision(lib):
+    a = acm.make_params((8, 8))
+    b = acm.make_params((16, 8), precision=acm.FP32_DEV)
+    arr = (acm.Params * 2)(a, b)
+    h = ctypes.c_void_p()
+    assert lib.acm_batch_create(arr, 2, ctypes.byref(h)) == acm.EINVAL
+    assert "share" in lib.acm_last_error(None).decode()
+
+
+def test_null_handle_calls_fail_cleanly(lib):
+    assert lib.acm_step(None, 1) == acm.EINVAL
+    assert lib.acm_sync(None) == acm.EINVAL
+    assert lib.acm_destroy(None) == acm.OK
+    assert lib.acm_nruns(None) == 0

@@ -1,0 +1,355 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle
+on the same seeded inputs.
+
+Tolerances:
+  * FP64 path: relative L2 <= 1e-12 per field (rho, u, v, w, phi) after the
+    stated number of steps (rho - rho0 at 1e-9, see assert_parity).  Both sides are FP64; they differ only
+    in rounding order (the kernels update the deviation rho - rho0 and the
+    velocity increment, the oracle absolute rho and rho u), ~1e-16 per step.
+  * FP32 deviation path: FP32 rounding (6e-8 relative) of O(1) velocities and
+    of the O(Ma^2) density deviation, accumulated over n steps of a
+    dissipative scheme, stays below ~1e-6 relative for u and ~3e-6 for the
+    density deviation at these sizes; tests use 2e-5 / 1e-4.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2012_03525_gb300 import acm, build
+from paper_2012_03525_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    acm.load()
+
+
+def rel_l2(a, b):
+    den = np.sqrt((b ** 2).sum())
+    num = np.sqrt(((a - b) ** 2).sum())
+    return float(num / den) if den > 0 else float(num)
+
+
+def _smooth(rng, shape, kmax2=9):
+    f = rng.standard_normal(shape)
+    F = np.fft.fftn(f)
+    ks = np.meshgrid(*[np.fft.fftfreq(n) * n for n in shape], indexing="ij")
+    F[sum(k * k for k in ks) > kmax2] = 0
+    return np.ascontiguousarray(np.real(np.fft.ifftn(F)))
+
+
+def run_both(oracle_lib, shape, state, nsteps, gpu_kw=None, **kw):
+    """Advance ``state`` = [rho, u, v(, w)(, phi)] with the oracle and the GPU;
+    return (oracle_state, gpu_state) as lists [rho, u, v, w, phi]."""
+    co = oracle_lib
+    gpu_kw = gpu_kw or {}
+    dim = len(shape)
+    rho, u, v = [x.copy() for x in state[:3]]
+    w = state[3].copy() if dim == 3 else None
+    phi = state[-1].copy() if kw.get("two_phase") else None
+    p = co.make_params(shape, **kw)
+    co.step(p, rho, u, v, w, phi, nsteps=nsteps)
+    ref = [rho, u, v, w, phi]
+
+    prm = acm.make_params(shape, **kw, **{k: v for k, v in gpu_kw.items() if k == "precision"})
+    with acm.Solver(prm) as s:
+        for key, val in gpu_kw.get("tuning", {}).items():
+            s.set_tuning(key, val)
+        st = [x.copy() for x in state[:3]]
+        s.set_fields(st[0], st[1], st[2], state[3] if dim == 3 else None,
+                     state[-1] if kw.get("two_phase") else None)
+        s.step(nsteps)
+        got = list(s.fields())
+    return ref, got
+
+
+def assert_parity(ref, got, rho0=1.0, tol=TOL64, tol_rho=None):
+    """Per-field relative L2.  Density: the paper's variable is the absolute
+    rho (compared at ``tol``); its deviation rho - rho0 is compared at
+    ``tol_rho`` -- for FP64 1e-9, because the oracle stores absolute rho, whose
+    rounding (1.1e-16 per step) is ~3e-13 of a 3e-4 deviation per step."""
+    tol_rho = (1e-9 if tol <= TOL64 else tol) if tol_rho is None else tol_rho
+    if tol <= TOL64:
+        assert rel_l2(got[0], ref[0]) <= tol
+    assert rel_l2(got[0] - rho0, ref[0] - rho0) <= tol_rho, rel_l2(got[0] - rho0, ref[0] - rho0)
+    for k in (1, 2, 3, 4):
+        if ref[k] is not None and np.abs(ref[k]).max() > 0:
+            err = rel_l2(got[k], ref[k])
+            if k < 4:
+                # velocities below 1e-6 (Ma < 2e-6, e.g. capillary currents of a
+                # weak-tension drop) are compared against that floor: the
+                # rounding of the O(1) terms that cancel to give them is
+                # ~1e-16 absolute per step
+                floor = 1e-6 * math.sqrt(ref[k].size)
+                err = float(np.sqrt(((got[k] - ref[k]) ** 2).sum()) /
+                            max(np.sqrt((ref[k] ** 2).sum()), floor))
+            assert err <= tol, (k, err)
+
+
+# ------------------------------------------------------------------- 2D FP64
+def test_tgv64_fp64_1000_steps(oracle_lib):
+    """The 64^2 periodic decaying TGV (u0 = 0.02, nu = 0.01, k = 2 pi/64),
+    1000 steps, FP64: relative L2 <= 1e-12 against the oracle; E_k follows
+    exp(-2 nu k^2 t) per velocity component (exp(-4 nu k^2 t) for energy) and
+    mass is conserved exactly."""
+    n, u0, nu, steps = 64, 0.02, 0.01, 1000
+    state = list(wl.tgv2d(n, u0))
+    ref, got = run_both(oracle_lib, (n, n), state, steps, nu=nu)
+    assert_parity(ref, got)
+    k = 2 * math.pi / n
+    ue, ve = wl.tgv2d_exact(n, u0, nu, steps)
+    assert rel_l2(got[1], ue) < 2e-3
+    assert abs(got[0].sum() - state[0].sum()) < 1e-12 * state[0].sum()
+    with acm.Solver(acm.make_params((n, n), nu=nu)) as s:
+        s.set_fields(*state)
+        d0 = s.reduce()
+        s.step(steps)
+        d1 = s.reduce()
+    assert d1[4] / d0[4] == pytest.approx(math.exp(-4 * nu * k * k * steps), rel=5e-3)
+    assert abs(d1[0] - d0[0]) < 1e-12 * d0[0]
+
+
+@pytest.mark.parametrize("shape", [(77, 100), (8, 8), (16, 33), (1, 40), (130, 5)])
+def test_2d_periodic_random_fp64(oracle_lib, shape):
+    """Several tiles with ragged tails, grids smaller than one tile, single
+    rows: smooth random fields, 150 steps."""
+    rng = np.random.default_rng(sum(shape))
+    state = [1 + 0.01 * _smooth(rng, shape), 0.05 * _smooth(rng, shape),
+             0.05 * _smooth(rng, shape)]
+    ref, got = run_both(oracle_lib, shape, state, 150, nu=0.05, g=(1e-5, -2e-5, 0))
+    assert_parity(ref, got)
+
+
+@pytest.mark.parametrize("sat", [0, 1, 2])
+def test_2d_sat_ablation_fp64(oracle_lib, sat):
+    rng = np.random.default_rng(3)
+    shape = (40, 48)
+    state = [1 + 0.001 * _smooth(rng, shape), 0.02 * _smooth(rng, shape),
+             0.02 * _smooth(rng, shape)]
+    # masks 0 and 1 are unstable (Section 3.1): short runs, before the growth
+    # amplifies rounding differences
+    ref, got = run_both(oracle_lib, shape, state, 60 if sat == 2 else 20, nu=0.05, sat_mask=sat)
+    assert_parity(ref, got)
+
+
+@pytest.mark.parametrize("shape", [(67, 70), (33, 33), (36, 34), (4, 4), (50, 35)])
+def test_2d_cavity_walls_fp64(oracle_lib, shape):
+    """No-slip walls with a moving lid (Section 3.2 set-up) from rest, grids
+    whose edges fall at every tile offset."""
+    ny, nx = shape
+    rho, u, v = np.ones(shape), np.zeros(shape), np.zeros(shape)
+    u[-1, 1:-1] = 0.1
+    ref, got = run_both(oracle_lib, shape, [rho, u, v], 300, nu=0.05,
+                        bc=[1, 1, 1, 2, 0, 0], lid_u=(0.1, 0, 0))
+    assert_parity(ref, got)
+
+
+def test_2d_channel_walls_x_periodic_y_fp64(oracle_lib):
+    shape = (20, 37)
+    rng = np.random.default_rng(5)
+    state = [1 + 0.001 * _smooth(rng, shape), 0.01 * _smooth(rng, shape),
+             0.01 * _smooth(rng, shape)]
+    ref, got = run_both(oracle_lib, shape, state, 200, nu=0.08, bc=[1, 1, 0, 0, 0, 0],
+                        g=(0, 1e-5, 0))
+    assert_parity(ref, got)
+
+
+def test_poiseuille_exact_on_gpu():
+    """GPU reaches the exact discrete parabola u(j) = g/(2 nu) j (L - j)."""
+    ny, nx, nu, g = 17, 4, 0.1, 1e-5
+    with acm.Solver(acm.make_params((ny, nx), nu=nu, g=(g, 0, 0), bc=[0, 0, 1, 1, 0, 0])) as s:
+        s.set_fields(np.ones((ny, nx)), np.zeros((ny, nx)), np.zeros((ny, nx)))
+        s.step(30000)
+        rho, u, v, _, _ = s.fields()
+    j = np.arange(ny)[:, None] * np.ones((1, nx))
+    exact = g / (2 * nu) * j * (ny - 1 - j)
+    assert np.abs(u - exact).max() < 1e-9 * exact.max()
+    assert np.abs(rho - 1).max() < 1e-14
+
+
+# ------------------------------------------------------------------- 3D
+@pytest.mark.parametrize("shape,tuning", [
+    ((33, 36, 40), {}),
+    ((20, 17, 70), {acm.TUNE_ZCHUNKS: 3}),
+    ((12, 40, 33), {acm.TUNE_ZCHUNKS: 12, acm.TUNE_T3Y: 16}),
+    ((1, 8, 8), {}),
+    ((5, 3, 2), {acm.TUNE_ZCHUNKS: 2}),
+])
+def test_3d_periodic_random_fp64(oracle_lib, shape, tuning):
+    rng = np.random.default_rng(sum(shape))
+    state = [1 + 0.01 * _smooth(rng, shape, 6)] + [0.04 * _smooth(rng, shape, 6) for _ in range(3)]
+    ref, got = run_both(oracle_lib, shape, state, 60, gpu_kw={"tuning": tuning}, nu=0.05,
+                        g=(1e-5, 2e-5, -1e-5))
+    assert_parity(ref, got)
+
+
+def test_3d_tgv_fp32_deviation(oracle_lib):
+    """FP32 deviation storage against the FP64 oracle on a 48^3 TGV."""
+    n = 48
+    state = list(wl.tgv3d(n, 0.05))
+    nu = wl.tgv3d_nu(n, 0.05, 100.0)
+    ref, got = run_both(oracle_lib, (n, n, n), state, 200, gpu_kw={"precision": acm.FP32_DEV},
+                        nu=nu)
+    assert_parity(ref, got, tol=2e-5, tol_rho=1e-4)
+
+
+def test_3d_tgv_fp64_matches_oracle(oracle_lib):
+    n = 40
+    state = list(wl.tgv3d(n, 0.05))
+    ref, got = run_both(oracle_lib, (n, n, n), state, 100, nu=wl.tgv3d_nu(n, 0.05, 100.0))
+    assert_parity(ref, got)
+
+
+def test_2d_fp32_deviation(oracle_lib):
+    n = 96
+    state = list(wl.tgv2d(n, 0.05))
+    ref, got = run_both(oracle_lib, (n, n), state, 500, gpu_kw={"precision": acm.FP32_DEV},
+                        nu=0.02)
+    assert_parity(ref, got, tol=2e-5, tol_rho=1e-4)
+
+
+# ------------------------------------------------------------------- two-phase
+@pytest.mark.parametrize("shape", [(70, 90), (40, 40), (17, 50)])
+def test_two_phase_drop_fp64(oracle_lib, shape):
+    ny, nx = shape
+    X, Y = np.meshgrid(np.arange(nx) - (nx - 1) / 2, np.arange(ny) - (ny - 1) / 2)
+    phi = -np.tanh(2 * (np.hypot(X / nx, Y / ny) * min(shape) - 0.3 * min(shape)) / 4.0)
+    rho, u, v = np.ones(shape), np.zeros(shape), np.zeros(shape)
+    rng = np.random.default_rng(9)
+    u = u + 0.002 * _smooth(rng, shape)
+    ref, got = run_both(oracle_lib, shape, [rho, u, v, phi], 120, nu=0.1, two_phase=True,
+                        sigma=1e-2, W=4.0, M=0.3)
+    assert_parity(ref, got)
+
+
+def test_two_phase_drop_fp32(oracle_lib):
+    rho, u, v, phi = wl.drop2d(64, 18.0, 4.0, eps=0.08)
+    ref, got = run_both(oracle_lib, (64, 64), [rho, u, v, phi], 300,
+                        gpu_kw={"precision": acm.FP32_DEV}, nu=0.1, two_phase=True, sigma=1e-2,
+                        W=4.0, M=0.3)
+    assert rel_l2(got[4], ref[4]) < 1e-6
+    assert rel_l2(got[1], ref[1]) < 1e-3  # velocities are O(1e-5) spurious currents
+    assert rel_l2(got[0] - 1, ref[0] - 1) < 1e-3
+
+
+# ------------------------------------------------------------------- batched
+def test_batched_two_phase_runs_match_oracle_each(oracle_lib):
+    """Five uneven runs in one batch (one persistent launch per step); every
+    run equals its own oracle run."""
+    co = oracle_lib
+    runs = [(40, 11.0, 0.05, 3e-3), (67, 20.0, 0.0, 1e-2), (33, 9.0, 0.1, 1e-4),
+            (90, 25.0, 0.07, 5e-3), (16, 5.0, 0.02, 2e-3)]
+    params, states = [], []
+    for n, R, eps, sigma in runs:
+        params.append(acm.make_params((n, n), nu=0.1, two_phase=True, sigma=sigma, W=4.0, M=0.1))
+        states.append(wl.drop2d(n, R, 4.0, eps=eps))
+    steps = 80
+    with acm.Solver(params) as s:
+        for r, st in enumerate(states):
+            s.set_fields(st[0], st[1], st[2], None, st[3], run=r)
+        s.step(steps)
+        for r, (n, R, eps, sigma) in enumerate(runs):
+            got = list(s.fields(run=r))
+            rho, u, v, phi = [x.copy() for x in states[r]]
+            p = co.make_params((n, n), nu=0.1, two_phase=True, sigma=sigma, W=4.0, M=0.1)
+            co.step(p, rho, u, v, None, phi, nsteps=steps)
+            assert_parity([rho, u, v, None, phi], got)
+        red = s.reduce()
+    assert red.shape == (5, 8)
+    for r, (n, *_rest) in enumerate(runs):
+        assert red[r, 0] == pytest.approx(states[r][0].sum(), rel=1e-13)
+
+
+def test_batched_single_phase_mixed_boundaries(oracle_lib):
+    co = oracle_lib
+    specs = [((24, 31), [0, 0, 0, 0, 0, 0]), ((40, 40), [1, 1, 1, 2, 0, 0]),
+             ((9, 50), [0, 0, 1, 1, 0, 0])]
+    rng = np.random.default_rng(11)
+    params, states = [], []
+    for shape, bc in specs:
+        params.append(acm.make_params(shape, nu=0.05, bc=bc, lid_u=(0.05, 0, 0)))
+        st = [1 + 0.001 * _smooth(rng, shape), 0.01 * _smooth(rng, shape),
+              0.01 * _smooth(rng, shape)]
+        states.append(st)
+    with acm.Solver(params) as s:
+        for r, st in enumerate(states):
+            s.set_fields(*st, run=r)
+        s.step(100)
+        for r, (shape, bc) in enumerate(specs):
+            got = list(s.fields(run=r))
+            rho, u, v = [x.copy() for x in states[r]]
+            co.step(co.make_params(shape, nu=0.05, bc=bc, lid_u=(0.05, 0, 0)), rho, u, v,
+                    nsteps=100)
+            assert_parity([rho, u, v, None, None], got)
+
+
+# ------------------------------------------------------------------- diagnostics
+@pytest.mark.parametrize("shape,prec", [((50, 61), acm.FP64), ((9, 20, 24), acm.FP64),
+                                        ((33, 40, 24), acm.FP32_DEV)])
+def test_reductions_match_oracle(oracle_lib, shape, prec):
+    co = oracle_lib
+    rng = np.random.default_rng(2)
+    st = [1 + 0.01 * _smooth(rng, shape)] + [0.03 * _smooth(rng, shape) for _ in shape]
+    with acm.Solver(acm.make_params(shape, nu=0.05, precision=prec)) as s:
+        s.set_fields(*st)
+        f0 = s.fields()
+        r0 = s.reduce()
+        s.step(3)
+        prev = s.fields()
+        s.step(1)
+        cur = s.fields()
+        r1 = s.reduce()
+    p = co.make_params(shape, nu=0.05)
+    w = cur[3] if len(shape) == 3 else None
+    pw = prev[3] if len(shape) == 3 else None
+    o1 = co.reduce(p, cur[0], cur[1], cur[2], w, prev=(prev[1], prev[2], pw))
+    o0 = co.reduce(p, f0[0], f0[1], f0[2], f0[3] if len(shape) == 3 else None)
+    tol = 1e-12 if prec == acm.FP64 else 1e-6
+    assert r0[0] == pytest.approx(o0[0], rel=1e-13)
+    for q in (0, 1, 2, 4):
+        assert r1[q] == pytest.approx(o1[q], rel=tol, abs=1e-13 * abs(o1[0]))
+    assert r1[5] == pytest.approx(o1[5], rel=1e-9)
+    assert r1[6] == pytest.approx(o1[6], rel=1e-12)
+    assert r1[7] == 0
+    assert r0[5] == 0.0
+
+
+def test_blow_up_reported_as_unstable():
+    """No SATs (Section 3.1 ablation) on grid-scale noise blows up; the next
+    synchronising call reports ACM_EUNSTABLE and further steps are refused."""
+    rng = np.random.default_rng(0)
+    shape = (32, 32)
+    with acm.Solver(acm.make_params(shape, nu=0.0, sat_mask=0)) as s:
+        s.set_fields(1 + 0.1 * rng.standard_normal(shape), 0.3 * rng.standard_normal(shape),
+                     0.3 * rng.standard_normal(shape))
+        s.step(3000)
+        with pytest.raises(acm.AcmError) as e:
+            s.sync()
+        assert e.value.status == acm.EUNSTABLE
+        with pytest.raises(acm.AcmError):
+            s.step(1)
+        # fields can be re-set, which clears the error
+        s.set_fields(np.ones(shape), np.zeros(shape), np.zeros(shape))
+        s.step(2)
+        s.sync()
+
+
+def test_graph_and_direct_launch_bitwise_equal():
+    rng = np.random.default_rng(4)
+    shape = (10, 24, 40)
+    st = [1 + 0.01 * _smooth(rng, shape)] + [0.03 * _smooth(rng, shape) for _ in range(3)]
+    out = []
+    for gsteps in (0, 16):
+        with acm.Solver(acm.make_params(shape, nu=0.05, precision=acm.FP32_DEV)) as s:
+            s.set_tuning(acm.TUNE_GRAPH_STEPS, gsteps)
+            s.set_fields(*st)
+            s.step(37)
+            out.append(s.fields())
+    for a, b in zip(out[0][:4], out[1][:4]):
+        assert np.array_equal(a, b)
