@@ -196,7 +196,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--zchunks", type=int, default=env_int("ACM_ZCHUNKS", 0))
-    ap.add_argument("--t3y", type=int, default=env_int("ACM_T3Y", 8))
+    ap.add_argument("--t3y", type=int, default=env_int("ACM_T3Y", 16))
     ap.add_argument("--n", type=int, default=N3,
                     help="grid side (profiling runs use a smaller cube; the bench line is 256)")
     args = ap.parse_args()

@@ -150,7 +150,7 @@ acm_status acm_reduce_mass(acm_handle *h, double *out);
  * Changing a knob drops captured graphs.  Returns ACM_EINVAL for an unknown
  * key or an out-of-range value. */
 enum {
-    ACM_TUNE_ZCHUNKS = 1,     /* 3D: z-chunks per x-y column (>= 1; 0 = heuristic) */
+    ACM_TUNE_ZCHUNKS = 1,     /* 3D: z-chunks per x-y column (>= 1; 0 = chunks of 16 planes) */
     ACM_TUNE_T3Y = 2,         /* 3D: tile height in y, 8 or 16 */
     ACM_TUNE_GRAPH_STEPS = 3, /* steps per captured CUDA graph, even, >= 2; 0 disables graphs */
     ACM_TUNE_BLOCKS = 4       /* 2D: persistent CTAs per launch (0 = fill the GPU) */

@@ -358,18 +358,9 @@ template <typename T>
 cudaError_t one_step(acm_handle *h, int from)
 {
     Fields<T> in = fields_of<T>(h, from), out = fields_of<T>(h, 1 - from);
-    if (h->dim == 3) {
-        const RunDesc &R = h->runs[0];
-        int zc = h->tune.zchunks;
-        if (zc <= 0) {
-            // fill the GPU with about one wave of CTAs
-            const long long cols = (long long)((R.nx + T3X - 1) / T3X) *
-                                   ((R.ny + h->tune.t3y - 1) / h->tune.t3y);
-            const long long slots = (long long)h->sms * step3d_max_blocks_per_sm<T>(h->tune.t3y);
-            zc = (int)std::max<long long>(1, std::min<long long>(R.nz, (slots + cols - 1) / cols));
-        }
-        return launch_step3d<T>(h->maps[from], out, R, h->derr, zc, h->tune.t3y, h->stream);
-    }
+    if (h->dim == 3)
+        return launch_step3d<T>(h->maps[from], out, h->runs[0], h->derr, h->tune.zchunks,
+                                h->tune.t3y, h->sms, h->stream);
     int blocks = h->tune.blocks;
     if (blocks <= 0) blocks = h->sms * step2d_max_blocks_per_sm<T>(h->two_phase);
     return launch_step2d<T>(h->druns, h->dwork, h->nwork, h->two_phase, in, out, h->derr, blocks,

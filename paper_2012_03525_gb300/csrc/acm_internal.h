@@ -76,8 +76,8 @@ constexpr int T3PAD = 2;     // ghost layers in x and y of the 3D layout
 constexpr int T3SLOTS = 5;   // input planes resident/in flight per CTA
 
 struct Tuning {
-    int zchunks = 0;       // 3D: z-chunks per column (0 = heuristic)
-    int t3y = 8;           // 3D: tile height (8 or 16)
+    int zchunks = 0;       // 3D: z-chunks per column (0 = chunks of 16 planes)
+    int t3y = 16;          // 3D: tile height (8 or 16)
     int graph_steps = 64;  // steps per captured CUDA graph (even)
     int blocks = 0;        // 2D: persistent CTAs (0 = occupancy x SMs)
 };
@@ -92,7 +92,7 @@ int step2d_max_blocks_per_sm(int two_phase);
 
 template <typename T>
 cudaError_t launch_step3d(const CUtensorMap *maps_in, Fields<T> out, const RunDesc &run,
-                          unsigned *derr, int zchunks, int t3y, cudaStream_t s);
+                          unsigned *derr, int zchunks, int t3y, int sms, cudaStream_t s);
 template <typename T>
 int step3d_max_blocks_per_sm(int t3y);
 

@@ -3,20 +3,31 @@
 // grids, single phase.
 //
 // Design (one kernel per step, HBM-bound):
-//   * Each CTA owns a T3X x TY column of the x-y plane and marches along z
-//     over a chunk of planes.  Input planes of rho', u, v, w (with a 2-node
-//     x-y halo) are staged in shared memory by TMA tiled loads
-//     (cp.async.bulk.tensor.3d) into a ring of T3SLOTS plane slots; the load
-//     of plane z+3 is in flight while plane z is computed.
-//   * Eq. (2.10) is evaluated on the plane z+1 grown by one node and kept in a
-//     ring of three Delta-rho planes, so d_a rho^{n+1} - d_a rho^n of
-//     Eq. (2.11) is a centred difference of Delta rho read from shared memory.
+//   * Each CTA owns a 32 x TY column of the x-y plane and marches along z over
+//     a chunk of planes; each thread owns two y-adjacent nodes of the column.
+//   * Input planes of rho', u, v, w (with a 2-node x-y halo) are staged in
+//     shared memory by TMA tiled loads (cp.async.bulk.tensor.3d) into a ring
+//     of NSLOT plane slots; loads run up to NSLOT-3 planes ahead of the one
+//     the compute waits for.
+//   * A thread keeps the values of its own two nodes on planes z-1..z+2 in
+//     registers (a register queue along z), so z-neighbours never touch
+//     shared memory; the upper/lower node of the pair serve as each other's
+//     y-neighbour.
+//   * Eq. (2.10) is evaluated for plane z+1 on the tile grown by one node:
+//     the own nodes in registers, the one-node ring by 100 threads; Delta rho
+//     of the own nodes stays in a register queue (z-1, z, z+1), the tile plane
+//     goes to shared memory for the x/y neighbours, so
+//     d_a rho^{n+1} - d_a rho^n of Eq. (2.11) is a centred difference of
+//     Delta rho.
 //   * Eq. (2.11) for plane z; u^{n+1} = u + (RHS - Delta rho u) / rho^{n+1}.
 // Storage is padded by T3PAD ghost nodes in x and y (not in z).  Every output
 // node on the first/last two columns/rows is also written to its periodic
 // image in the ghost layers, so the next step's TMA boxes never wrap in x/y;
 // z wraps through the box coordinate.  Padding also keeps every box start on a
 // 16-byte boundary (x start = tile x0, a multiple of 32 elements).
+#include <algorithm>
+#include <type_traits>
+
 #include "acm_internal.h"
 
 namespace acm {
@@ -66,199 +77,331 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, i
 // bounded wait: ~ 2^22 polls (well over a second), then give up
 constexpr int WAIT_LIMIT = 1 << 22;
 
-template <typename T, int TY>
-struct Geo {
-    static constexpr int RW = T3X + 4, RH = TY + 4, PLANE = RW * RH;
-    static constexpr int PLANE_BYTES = ((PLANE * (int)sizeof(T) + 127) / 128) * 128;
-    static constexpr int RW1 = T3X + 2, RH1 = TY + 2, P1 = RW1 * RH1;
-    static constexpr int SD_BYTES = ((3 * P1 * (int)sizeof(T) + 127) / 128) * 128;
-    static constexpr int SMEM = T3SLOTS * 4 * PLANE_BYTES + SD_BYTES + 128;
-    static constexpr int NT = T3X * TY;
+template <typename T>
+struct Prec;
+template <>
+struct Prec<float> {
+    static constexpr int NSLOT = 5;
+    static constexpr int MINB = 3;  // CTAs per SM (of 256 threads) to aim for
+    static __device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+};
+template <>
+struct Prec<double> {
+    static constexpr int NSLOT = 4;
+    static constexpr int MINB = 1;
+    static __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 };
 
 template <typename T, int TY>
-__global__ void __launch_bounds__(T3X *TY)
+struct Geo {
+    static constexpr int NSLOT = Prec<T>::NSLOT;
+    static constexpr int RW = T3X + 4, RH = TY + 4, PLANE = RW * RH;
+    static constexpr int PLANE_BYTES = ((PLANE * (int)sizeof(T) + 127) / 128) * 128;
+    static constexpr int RW1 = T3X + 2, RH1 = TY + 2, P1 = RW1 * RH1;
+    static constexpr int NRING = 2 * T3X + 2 * RH1;  // one-node ring around the tile
+    static constexpr int PLANE_ELEMS = PLANE_BYTES / (int)sizeof(T);
+    static constexpr int SD_BYTES = ((2 * P1 * (int)sizeof(T) + 127) / 128) * 128;
+    static constexpr int BAR_OFFSET = NSLOT * 4 * PLANE_BYTES + SD_BYTES;
+    static constexpr int SMEM = BAR_OFFSET + 128;
+    static constexpr int NT = T3X * TY / 2;
+    static_assert(NRING <= NT, "ring points must fit one pass");
+};
+
+// values of the thread's two nodes (a = lower row, b = upper row) on one plane
+template <typename T>
+struct Col {
+    T r[2], u[2], v[2], w[2];
+};
+
+// Eq. (2.11) for one node from its 7-point neighbourhood (index order
+// C, E, W, N, S, U, D) of rho', u, v, w and Delta rho; returns the new state.
+template <typename T>
+__device__ __forceinline__ void node_update(const T (&r)[7], const T (&u)[7], const T (&v)[7],
+                                            const T (&w)[7], const T (&d)[7], T rho0, T hdt,
+                                            T hdtcs2, T nudt, T hsatm, T dt, T gx, T gy, T gz,
+                                            T &rn, T &un, T &vn, T &wn)
+{
+    T mx[7], my[7], mz[7];
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        const T q = rho0 + r[k];
+        mx[k] = q * u[k];
+        my[k] = q * v[k];
+        mz[k] = q * w[k];
+    }
+    // centred flux differences d_b(rho u_a u_b) (times 2) and Laplacians
+    const T fx = (mx[1] * u[1] - mx[2] * u[2]) + (mx[3] * v[3] - mx[4] * v[4]) +
+                 (mx[5] * w[5] - mx[6] * w[6]);
+    const T fy = (my[1] * u[1] - my[2] * u[2]) + (my[3] * v[3] - my[4] * v[4]) +
+                 (my[5] * w[5] - my[6] * w[6]);
+    const T fz = (mz[1] * u[1] - mz[2] * u[2]) + (mz[3] * v[3] - mz[4] * v[4]) +
+                 (mz[5] * w[5] - mz[6] * w[6]);
+    const T lx = (mx[1] + mx[2]) + (mx[3] + mx[4]) + (mx[5] + mx[6]) - T(6) * mx[0];
+    const T ly = (my[1] + my[2]) + (my[3] + my[4]) + (my[5] + my[6]) - T(6) * my[0];
+    const T lz = (mz[1] + mz[2]) + (mz[3] + mz[4]) + (mz[5] + mz[6]) - T(6) * mz[0];
+    const T rho1 = rho0 + r[0] + d[0];
+    const T inv = Prec<T>::recip(rho1);
+    const T fb = dt * rho1;
+    const T rx = -hdt * fx - hdtcs2 * (r[1] - r[2]) + nudt * lx - hsatm * (d[1] - d[2]) + fb * gx;
+    const T ry = -hdt * fy - hdtcs2 * (r[3] - r[4]) + nudt * ly - hsatm * (d[3] - d[4]) + fb * gy;
+    const T rz = -hdt * fz - hdtcs2 * (r[5] - r[6]) + nudt * lz - hsatm * (d[5] - d[6]) + fb * gz;
+    un = u[0] + (rx - d[0] * u[0]) * inv;
+    vn = v[0] + (ry - d[0] * v[0]) * inv;
+    wn = w[0] + (rz - d[0] * w[0]) * inv;
+    rn = r[0] + d[0];
+}
+
+template <int J>
+using IC = std::integral_constant<int, J>;
+
+// Write a node's periodic images in the ghost layers (both images exist when
+// the grid is narrower than 2 * T3PAD); only the threads on the first/last
+// T3PAD columns/rows call it.
+template <typename T>
+__device__ __forceinline__ void store_images(Fields<T> out, long long gi, int gx, int gy, int nx,
+                                          int ny, long long PX, T rn, T un, T vn, T wn)
+{
+    int xs[3], ys[3], nxs = 1, nys = 1;
+    xs[0] = 0;
+    ys[0] = 0;
+    if (gx < T3PAD) xs[nxs++] = nx;
+    if (gx >= nx - T3PAD) xs[nxs++] = -nx;
+    if (gy < T3PAD) ys[nys++] = ny;
+    if (gy >= ny - T3PAD) ys[nys++] = -ny;
+    for (int jy = 0; jy < nys; ++jy)
+        for (int jx = 0; jx < nxs; ++jx) {
+            if (jx == 0 && jy == 0) continue;
+            const long long gk = gi + (long long)ys[jy] * PX + xs[jx];
+            out.f[F_R][gk] = rn;
+            out.f[F_U][gk] = un;
+            out.f[F_V][gk] = vn;
+            out.f[F_W][gk] = wn;
+        }
+}
+
+template <typename T, int TY>
+__global__ void __launch_bounds__(T3X *TY / 2, Prec<T>::MINB * 16 / TY)
     k_step3d(const __grid_constant__ CUtensorMap mr, const __grid_constant__ CUtensorMap mu_,
              const __grid_constant__ CUtensorMap mv, const __grid_constant__ CUtensorMap mw,
              Fields<T> out, const __grid_constant__ RunDesc R, int zc, unsigned *err)
 {
     using G = Geo<T, TY>;
+    constexpr int NSLOT = G::NSLOT, RW = G::RW, RW1 = G::RW1, PE = G::PLANE_ELEMS, P1 = G::P1;
     extern __shared__ __align__(128) unsigned char smem[];
-    T *sd = reinterpret_cast<T *>(smem + T3SLOTS * 4 * G::PLANE_BYTES);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + T3SLOTS * 4 * G::PLANE_BYTES + G::SD_BYTES);
-    int *s_abort = reinterpret_cast<int *>(bar + T3SLOTS);
-    auto plane = [&](int slot, int f) -> T * {
-        return reinterpret_cast<T *>(smem + (slot * 4 + f) * G::PLANE_BYTES);
-    };
+    T *S = reinterpret_cast<T *>(smem);        // plane (slot s, field f) at (4 s + f) PE
+    T *SD = S + NSLOT * 4 * PE;                  // two Delta-rho windows of P1
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + G::BAR_OFFSET);
+    int *s_abort = reinterpret_cast<int *>(bar + NSLOT);
 
     const int tid = threadIdx.x;
-    const int tx = tid % T3X, ty = tid / T3X;
+    const int tx = tid & 31, ty2 = tid >> 5;
     const int nx = R.nx, ny = R.ny, nz = R.nz;
-    const int x0 = blockIdx.x * T3X, y0 = blockIdx.y * TY;
-    const int zbeg = blockIdx.z * zc;
-    const int zend = min(zbeg + zc, nz);
-    if (zbeg >= zend) return;
+    const int ncx = (nx + T3X - 1) / T3X;
+    const int nzc = (nz + zc - 1) / zc;  // chunks per column
+    const int nitems = ncx * ((ny + TY - 1) / TY) * nzc;
+    if ((int)blockIdx.x >= nitems) return;
+
     const T *C = coefs<T>(R);
     const T rho0 = C[C_RHO0], dt = C[C_DT], cs2 = C[C_CS2], nudt = C[C_NUDT];
-    const T satc = C[C_SATC], satm = C[C_SATM];
-    const T gxb = C[C_GX], gyb = C[C_GY], gzb = C[C_GZ];
+    const T hdt = T(0.5) * dt, hdtcs2 = T(0.5) * dt * cs2;
+    const T satc = C[C_SATC], hsatm = T(0.5) * C[C_SATM];
+    const T gfx = C[C_GX], gfy = C[C_GY], gfz = C[C_GZ];
     constexpr uint32_t TX_BYTES = 4u * G::PLANE * sizeof(T);
 
     if (tid == 0) {
-        for (int s = 0; s < T3SLOTS; ++s) mbar_init(&bar[s], 1);
+        for (int s = 0; s < NSLOT; ++s) mbar_init(&bar[s], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         *s_abort = 0;
     }
     __syncthreads();
 
-    // plane zz (zbeg-2 <= zz <= zend+1) lives in slot (zz - zbeg + 2) % T3SLOTS
-    auto issue = [&](int zz) {
-        const int k = zz - zbeg + 2;
-        const int s = k % T3SLOTS;
-        int zw = zz % nz;
+    // own nodes: offsets in a plane window and in a Delta-rho window
+    const int ya = 2 * ty2;
+    const int ca = (ya + 2) * RW + (tx + 2), cb = ca + RW;
+    const int da = (ya + 1) * RW1 + (tx + 1), db = da + RW1;
+    // ring point of this thread (tid < NRING): offsets in both windows
+    int ring_d = -1, ring_c = 0;
+    if (tid < G::NRING) {
+        int lx, ly;
+        if (tid < T3X) { lx = tid + 1; ly = 0; }
+        else if (tid < 2 * T3X) { lx = tid - T3X + 1; ly = G::RH1 - 1; }
+        else if (tid < 2 * T3X + G::RH1) { lx = 0; ly = tid - 2 * T3X; }
+        else { lx = RW1 - 1; ly = tid - 2 * T3X - G::RH1; }
+        ring_d = ly * RW1 + lx;
+        ring_c = (ly + 1) * RW + (lx + 1);
+    }
+    const long long PX = R.px, PXY = R.px * R.py;
+
+    // Every chunk puts plane zbeg-2 in slot 0, so plane p sits in slot
+    // (p - zbeg + 2) % NSLOT; the loop below is unrolled by NSLOT so every
+    // slot index is a compile-time constant.  Bit s of `phase` is the parity
+    // of the next completion of slot s's barrier.
+    uint32_t phase = 0;
+    auto issue = [&](int s, int p, int x0, int y0) {
+        int zw = p % nz;
         if (zw < 0) zw += nz;
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_expect_tx(&bar[s], TX_BYTES);
-        tma_load_3d(plane(s, F_R), &mr, x0, y0, zw, &bar[s]);
-        tma_load_3d(plane(s, F_U), &mu_, x0, y0, zw, &bar[s]);
-        tma_load_3d(plane(s, F_V), &mv, x0, y0, zw, &bar[s]);
-        tma_load_3d(plane(s, F_W), &mw, x0, y0, zw, &bar[s]);
+        T *dst = S + s * 4 * PE;
+        tma_load_3d(dst, &mr, x0, y0, zw, &bar[s]);
+        tma_load_3d(dst + PE, &mu_, x0, y0, zw, &bar[s]);
+        tma_load_3d(dst + 2 * PE, &mv, x0, y0, zw, &bar[s]);
+        tma_load_3d(dst + 3 * PE, &mw, x0, y0, zw, &bar[s]);
     };
-    auto wait = [&](int zz) {
-        const int k = zz - zbeg + 2;
-        const int s = k % T3SLOTS;
-        const uint32_t par = (uint32_t)((k / T3SLOTS) & 1);
+    auto wait = [&](int s) {
+        const uint32_t par = (phase >> s) & 1u;
+        phase ^= 1u << s;
         for (int it = 0; it < WAIT_LIMIT; ++it)
             if (mbar_try_wait(&bar[s], par)) return;
         *s_abort = 1;
         atomicOr(err, ERR_TIMEOUT);
     };
-    auto slot_of = [&](int zz) { return (zz - zbeg + 2) % T3SLOTS; };
-    auto sdp = [&](int zz) { return sd + ((zz - zbeg + 3) % 3) * G::P1; };
-
-    // Eq. (2.10) on plane zz grown by one node: needs planes zz-1, zz, zz+1
-    auto delta_rho = [&](int zz) {
-        const int sm = slot_of(zz - 1), s0 = slot_of(zz), sp = slot_of(zz + 1);
-        const T *r0 = plane(s0, F_R), *u0 = plane(s0, F_U), *v0 = plane(s0, F_V);
-        const T *rm = plane(sm, F_R), *wm = plane(sm, F_W);
-        const T *rp = plane(sp, F_R), *wp = plane(sp, F_W);
-        T *dst = sdp(zz);
-        for (int i = tid; i < G::P1; i += G::NT) {
-            const int ly = i / G::RW1, lx = i - ly * G::RW1;
-            const int c = (ly + 1) * G::RW + (lx + 1);
-            const T div = T(0.5) * ((rho0 + r0[c + 1]) * u0[c + 1] - (rho0 + r0[c - 1]) * u0[c - 1]) +
-                          T(0.5) * ((rho0 + r0[c + G::RW]) * v0[c + G::RW] -
-                                    (rho0 + r0[c - G::RW]) * v0[c - G::RW]) +
-                          T(0.5) * ((rho0 + rp[c]) * wp[c] - (rho0 + rm[c]) * wm[c]);
-            const T lap = r0[c + 1] + r0[c - 1] + r0[c + G::RW] + r0[c - G::RW] + rp[c] + rm[c] -
-                          T(6) * r0[c];
-            dst[i] = -dt * div + satc * lap;
+    auto load_col = [&](int s, Col<T> &q) {
+        const T *P = S + s * 4 * PE;
+        q.r[0] = P[ca];
+        q.r[1] = P[cb];
+        q.u[0] = P[PE + ca];
+        q.u[1] = P[PE + cb];
+        q.v[0] = P[2 * PE + ca];
+        q.v[1] = P[2 * PE + cb];
+        q.w[0] = P[3 * PE + ca];
+        q.w[1] = P[3 * PE + cb];
+    };
+    // Eq. (2.10) on the plane in slot s0 (slots sm, sp hold planes -1, +1):
+    // own nodes from registers + smem, ring from smem; result to window dw.
+    auto delta_rho = [&](int sm, int s0, int sp, T *dw, const Col<T> &Cd, const Col<T> &C0,
+                         const Col<T> &Cu, T (&dout)[2]) {
+        const T *pr = S + s0 * 4 * PE, *pu = pr + PE, *pv = pr + 2 * PE;
+        {   // lower node a: N is node b
+            const T rE = pr[ca + 1], rW = pr[ca - 1], rS = pr[ca - RW], rN = C0.r[1];
+            const T div = ((rho0 + rE) * pu[ca + 1] - (rho0 + rW) * pu[ca - 1]) +
+                          ((rho0 + rN) * C0.v[1] - (rho0 + rS) * pv[ca - RW]) +
+                          ((rho0 + Cu.r[0]) * Cu.w[0] - (rho0 + Cd.r[0]) * Cd.w[0]);
+            const T lap = (rE + rW) + (rN + rS) + (Cu.r[0] + Cd.r[0]) - T(6) * C0.r[0];
+            dout[0] = satc * lap - hdt * div;
+        }
+        {   // upper node b: S is node a
+            const T rE = pr[cb + 1], rW = pr[cb - 1], rN = pr[cb + RW], rS = C0.r[0];
+            const T div = ((rho0 + rE) * pu[cb + 1] - (rho0 + rW) * pu[cb - 1]) +
+                          ((rho0 + rN) * pv[cb + RW] - (rho0 + rS) * C0.v[0]) +
+                          ((rho0 + Cu.r[1]) * Cu.w[1] - (rho0 + Cd.r[1]) * Cd.w[1]);
+            const T lap = (rE + rW) + (rN + rS) + (Cu.r[1] + Cd.r[1]) - T(6) * C0.r[1];
+            dout[1] = satc * lap - hdt * div;
+        }
+        dw[da] = dout[0];
+        dw[db] = dout[1];
+        if (ring_d >= 0) {
+            const int c = ring_c;
+            const T *rd = S + sm * 4 * PE, *wd = rd + 3 * PE;
+            const T *ru = S + sp * 4 * PE, *wu = ru + 3 * PE;
+            const T div = ((rho0 + pr[c + 1]) * pu[c + 1] - (rho0 + pr[c - 1]) * pu[c - 1]) +
+                          ((rho0 + pr[c + RW]) * pv[c + RW] - (rho0 + pr[c - RW]) * pv[c - RW]) +
+                          ((rho0 + ru[c]) * wu[c] - (rho0 + rd[c]) * wd[c]);
+            const T lap = (pr[c + 1] + pr[c - 1]) + (pr[c + RW] + pr[c - RW]) + (ru[c] + rd[c]) -
+                          T(6) * pr[c];
+            dw[ring_d] = satc * lap - hdt * div;
         }
     };
 
-    // prologue: planes zbeg-2 .. zbeg+2, Delta rho of zbeg-1 and zbeg
-    if (tid == 0)
-        for (int zz = zbeg - 2; zz <= zbeg + 2; ++zz) issue(zz);
-    wait(zbeg - 2);
-    wait(zbeg - 1);
-    wait(zbeg);
-    __syncthreads();
-    if (*s_abort) return;
-    delta_rho(zbeg - 1);
-    wait(zbeg + 1);
-    __syncthreads();
-    if (*s_abort) return;
-    delta_rho(zbeg);
+    bool nonfinite = false;
+    Col<T> Q[NSLOT];   // own-node values of the plane held in slot s
+    T D[NSLOT][2];     // own-node Delta rho of the plane held in slot s
 
-    const int gx = x0 + tx, gy = y0 + ty;
-    const bool owner = gx < nx && gy < ny;
-    const long long PX = R.px, PXY = R.px * R.py;
-    const long long base = R.off + (long long)(gy + T3PAD) * PX + (gx + T3PAD);
-    const bool edge = gx < T3PAD || gx >= nx - T3PAD || gy < T3PAD || gy >= ny - T3PAD;
-    const int c = (ty + 2) * G::RW + (tx + 2);
-    const int c1 = (ty + 1) * G::RW1 + (tx + 1);
+    for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+        // chunk: column col, planes [zbeg, zend)
+        const int col = item / nzc;
+        const int zbeg = (item - col * nzc) * zc;
+        const int zend = min(zbeg + zc, nz);
+        const int x0 = (col % ncx) * T3X, y0 = (col / ncx) * TY;
+        const int zlast = zend + 1;  // last plane this chunk needs
 
-    for (int z = zbeg; z < zend; ++z) {
-        __syncthreads();  // slot of plane z-2 and Delta-rho ring slot of z-2 are free
-        if (tid == 0 && z + 3 <= zend + 1) issue(z + 3);
-        wait(z + 2);
-        delta_rho(z + 1);  // harmless on stale data if the wait gave up
+        // prologue: planes zbeg-2 .. zbeg+NSLOT-3 into slots 0 .. NSLOT-1
+        if (tid == 0)
+            for (int k = 0; k < NSLOT && zbeg - 2 + k <= zlast; ++k) issue(k, zbeg - 2 + k, x0, y0);
+        for (int k = 0; k < 4; ++k) wait(k);
         __syncthreads();
         if (*s_abort) break;
+        load_col(0, Q[0]);
+        load_col(1, Q[1]);
+        load_col(2, Q[2]);
+        load_col(3, Q[3]);
+        delta_rho(0, 1, 2, SD + ((zbeg - 1) & 1) * P1, Q[0], Q[1], Q[2], D[1]);
+        delta_rho(1, 2, 3, SD + (zbeg & 1) * P1, Q[1], Q[2], Q[3], D[2]);
+        __syncthreads();  // plane zbeg-2 is no longer read
+        if (tid == 0 && zbeg + NSLOT - 2 <= zlast) issue(0, zbeg + NSLOT - 2, x0, y0);
 
-        if (owner) {
-            const int sm = slot_of(z - 1), s0 = slot_of(z), sp = slot_of(z + 1);
-            const T *r = plane(s0, F_R), *u = plane(s0, F_U), *v = plane(s0, F_V),
-                    *w = plane(s0, F_W);
-            const T *rm = plane(sm, F_R), *um = plane(sm, F_U), *vm = plane(sm, F_V),
-                    *wm = plane(sm, F_W);
-            const T *rp = plane(sp, F_R), *up = plane(sp, F_U), *vp = plane(sp, F_V),
-                    *wp = plane(sp, F_W);
-            const T *d0 = sdp(z), *dm = sdp(z - 1), *dp = sdp(z + 1);
-
-            const T r0 = r[c], u0 = u[c], v0 = v[c], w0 = w[c], dr = d0[c1];
-            // neighbour densities rho0 + rho'
-            const T qE = rho0 + r[c + 1], qW = rho0 + r[c - 1];
-            const T qN = rho0 + r[c + G::RW], qS = rho0 + r[c - G::RW];
-            const T qU = rho0 + rp[c], qD = rho0 + rm[c];
-            const T uE = u[c + 1], uW = u[c - 1], uN = u[c + G::RW], uS = u[c - G::RW],
-                    uU = up[c], uD = um[c];
-            const T vE = v[c + 1], vW = v[c - 1], vN = v[c + G::RW], vS = v[c - G::RW],
-                    vU = vp[c], vD = vm[c];
-            const T wE = w[c + 1], wW = w[c - 1], wN = w[c + G::RW], wS = w[c - G::RW],
-                    wU = wp[c], wD = wm[c];
-            const T q0 = rho0 + r0;
-            const T rho1 = q0 + dr;
-            const T inv = T(1) / rho1;
-            const T ddx = T(0.5) * (d0[c1 + 1] - d0[c1 - 1]);
-            const T ddy = T(0.5) * (d0[c1 + G::RW1] - d0[c1 - G::RW1]);
-            const T ddz = T(0.5) * (dp[c1] - dm[c1]);
-            // flux d_b(rho u_a u_b) + c_s^2 d_a rho', viscous nu Lap(rho u_a)
-            auto comp = [&](T aE, T aW, T aN, T aS, T aU, T aD, T a0, T dpress, T dd, T gb) {
-                const T mE = qE * aE, mW = qW * aW, mN = qN * aN, mS = qS * aS, mU = qU * aU,
-                        mD = qD * aD;
-                const T flux = T(0.5) * (mE * uE - mW * uW) + T(0.5) * (mN * vN - mS * vS) +
-                               T(0.5) * (mU * wU - mD * wD) + cs2 * dpress;
-                const T lapm = mE + mW + mN + mS + mU + mD - T(6) * (q0 * a0);
-                const T rhs = -dt * flux + nudt * lapm - satm * dd + dt * rho1 * gb;
-                return a0 + (rhs - dr * a0) * inv;
-            };
-            const T un = comp(uE, uW, uN, uS, uU, uD, u0, T(0.5) * (r[c + 1] - r[c - 1]), ddx, gxb);
-            const T vn = comp(vE, vW, vN, vS, vU, vD, v0, T(0.5) * (r[c + G::RW] - r[c - G::RW]),
-                              ddy, gyb);
-            const T wn = comp(wE, wW, wN, wS, wU, wD, w0, T(0.5) * (rp[c] - rm[c]), ddz, gzb);
-            const T rn = r0 + dr;
-
-            // write the node; threads on the first/last T3PAD columns/rows also
-            // write its periodic images in the ghost layers (both images exist
-            // when the grid is narrower than 2 * T3PAD)
-            const long long gi = base + (long long)z * PXY;
+        const int gx = x0 + tx, gya = y0 + ya, gyb = gya + 1;
+        const bool own_a = gx < nx && gya < ny, own_b = gx < nx && gyb < ny;
+        const bool edge = gx < T3PAD || gx >= nx - T3PAD || gya < T3PAD || gyb >= ny - T3PAD;
+        const long long base_a = R.off + (long long)(gya + T3PAD) * PX + (gx + T3PAD);
+        auto store = [&](long long gi, int gy, T rn, T un, T vn, T wn) {
             out.f[F_R][gi] = rn;
             out.f[F_U][gi] = un;
             out.f[F_V][gi] = vn;
             out.f[F_W][gi] = wn;
-            if (edge) {
-                int xs[3], ys[3], nxs = 1, nys = 1;
-                xs[0] = 0;
-                ys[0] = 0;
-                if (gx < T3PAD) xs[nxs++] = nx;
-                if (gx >= nx - T3PAD) xs[nxs++] = -nx;
-                if (gy < T3PAD) ys[nys++] = ny;
-                if (gy >= ny - T3PAD) ys[nys++] = -ny;
-                for (int jy = 0; jy < nys; ++jy)
-                    for (int jx = 0; jx < nxs; ++jx) {
-                        if (jx == 0 && jy == 0) continue;
-                        const long long gk = gi + (long long)ys[jy] * PX + xs[jx];
-                        out.f[F_R][gk] = rn;
-                        out.f[F_U][gk] = un;
-                        out.f[F_V][gk] = vn;
-                        out.f[F_W][gk] = wn;
-                    }
+            if (edge) store_images<T>(out, gi, gx, gy, nx, ny, PX, rn, un, vn, wn);
+            // a non-finite value in any field makes the sum non-finite
+            nonfinite |= !isfinite(rn + un + vn + wn);
+        };
+
+        // one z step for plane z = zg + J, with (zg - zbeg) a multiple of NSLOT
+        auto step = [&](auto JC, int zg) {
+            constexpr int J = decltype(JC)::value;
+            constexpr int SM = (J + 1) % NSLOT, S0 = (J + 2) % NSLOT;  // planes z-1, z
+            constexpr int S1 = (J + 3) % NSLOT, S2 = (J + 4) % NSLOT;  // planes z+1, z+2
+            const int z = zg + J;
+            __syncthreads();  // plane z-1 and the Delta-rho window of z-1 are free
+            if (tid == 0 && z + NSLOT - 1 <= zlast) issue(SM, z + NSLOT - 1, x0, y0);
+            wait(S2);
+            load_col(S2, Q[S2]);
+            // harmless on stale data if the wait gave up
+            delta_rho(S0, S1, S2, SD + ((z + 1) & 1) * P1, Q[S0], Q[S1], Q[S2], D[S1]);
+            __syncthreads();
+            if (*s_abort) return;
+
+            const T *pr = S + S0 * 4 * PE, *pu = pr + PE, *pv = pr + 2 * PE, *pw = pr + 3 * PE;
+            const T *dz = SD + (z & 1) * P1;
+            const Col<T> &Xm = Q[SM], &X0 = Q[S0], &Xp = Q[S1];
+            T rn, un, vn, wn;
+            {   // lower node a: N neighbour is node b
+                const T r[7] = {X0.r[0], pr[ca + 1], pr[ca - 1], X0.r[1], pr[ca - RW], Xp.r[0], Xm.r[0]};
+                const T u[7] = {X0.u[0], pu[ca + 1], pu[ca - 1], X0.u[1], pu[ca - RW], Xp.u[0], Xm.u[0]};
+                const T v[7] = {X0.v[0], pv[ca + 1], pv[ca - 1], X0.v[1], pv[ca - RW], Xp.v[0], Xm.v[0]};
+                const T w[7] = {X0.w[0], pw[ca + 1], pw[ca - 1], X0.w[1], pw[ca - RW], Xp.w[0], Xm.w[0]};
+                const T d[7] = {D[S0][0], dz[da + 1], dz[da - 1], D[S0][1], dz[da - RW1], D[S1][0], D[SM][0]};
+                node_update<T>(r, u, v, w, d, rho0, hdt, hdtcs2, nudt, hsatm, dt, gfx, gfy, gfz,
+                               rn, un, vn, wn);
+                if (own_a) store(base_a + (long long)z * PXY, gya, rn, un, vn, wn);
             }
-            if (!isfinite(rn) || !isfinite(un) || !isfinite(vn) || !isfinite(wn))
-                atomicOr(err, ERR_NONFINITE);
+            {   // upper node b: S neighbour is node a
+                const T r[7] = {X0.r[1], pr[cb + 1], pr[cb - 1], pr[cb + RW], X0.r[0], Xp.r[1], Xm.r[1]};
+                const T u[7] = {X0.u[1], pu[cb + 1], pu[cb - 1], pu[cb + RW], X0.u[0], Xp.u[1], Xm.u[1]};
+                const T v[7] = {X0.v[1], pv[cb + 1], pv[cb - 1], pv[cb + RW], X0.v[0], Xp.v[1], Xm.v[1]};
+                const T w[7] = {X0.w[1], pw[cb + 1], pw[cb - 1], pw[cb + RW], X0.w[0], Xp.w[1], Xm.w[1]};
+                const T d[7] = {D[S0][1], dz[db + 1], dz[db - 1], dz[db + RW1], D[S0][0], D[S1][1], D[SM][1]};
+                node_update<T>(r, u, v, w, d, rho0, hdt, hdtcs2, nudt, hsatm, dt, gfx, gfy, gfz,
+                               rn, un, vn, wn);
+                if (own_b) store(base_a + PX + (long long)z * PXY, gyb, rn, un, vn, wn);
+            }
+        };
+
+        for (int zg = zbeg; zg < zend; zg += NSLOT) {
+            step(IC<0>{}, zg);
+            if (zg + 1 >= zend || *s_abort) break;
+            step(IC<1>{}, zg);
+            if (zg + 2 >= zend || *s_abort) break;
+            step(IC<2>{}, zg);
+            if (zg + 3 >= zend || *s_abort) break;
+            step(IC<3>{}, zg);
+            if (NSLOT > 4) {
+                if (zg + 4 >= zend || *s_abort) break;
+                step(IC<(NSLOT > 4 ? 4 : 0)>{}, zg);
+            }
         }
+        __syncthreads();  // every read of this chunk's planes is done
+        if (*s_abort) break;
     }
+    if (nonfinite) atomicOr(err, ERR_NONFINITE);
 }
 
 template <typename T, int TY>
@@ -280,15 +423,22 @@ int max_blocks()
 
 template <typename T, int TY>
 cudaError_t launch(const CUtensorMap *m, Fields<T> out, const RunDesc &run, unsigned *derr,
-                   int zchunks, cudaStream_t s)
+                   int zchunks, int sms, cudaStream_t s)
 {
     using G = Geo<T, TY>;
-    max_blocks<T, TY>();
-    if (zchunks < 1) zchunks = 1;
-    if (zchunks > run.nz) zchunks = run.nz;
-    const int zc = (run.nz + zchunks - 1) / zchunks;
-    dim3 grid((run.nx + T3X - 1) / T3X, (run.ny + TY - 1) / TY, (run.nz + zc - 1) / zc);
-    k_step3d<T, TY><<<grid, G::NT, G::SMEM, s>>>(m[0], m[1], m[2], m[3], out, run, zc, derr);
+    const int per_sm = max_blocks<T, TY>();
+    // chunks of zc planes; by default 16 (short enough for many CTAs, long
+    // enough that the 4 extra planes per chunk cost little)
+    const int nzc = zchunks > 0 ? std::min(zchunks, run.nz) : std::max(1, (run.nz + 15) / 16);
+    const int zc = (run.nz + nzc - 1) / nzc;
+    const long long items = (long long)((run.nx + T3X - 1) / T3X) * ((run.ny + TY - 1) / TY) *
+                            ((run.nz + zc - 1) / zc);
+    // persistent CTAs walk the chunks in (column, z-chunk) order, so CTAs
+    // resident together work on neighbouring columns at the same depths and
+    // share their halo planes through L2
+    const long long grid = std::min<long long>(items, (long long)sms * per_sm);
+    k_step3d<T, TY><<<(unsigned)grid, G::NT, G::SMEM, s>>>(m[0], m[1], m[2], m[3], out, run, zc,
+                                                          derr);
     return cudaGetLastError();
 }
 
@@ -297,21 +447,21 @@ cudaError_t launch(const CUtensorMap *m, Fields<T> out, const RunDesc &run, unsi
 template <typename T>
 int step3d_max_blocks_per_sm(int t3y)
 {
-    return t3y == 16 ? max_blocks<T, 16>() : max_blocks<T, 8>();
+    return t3y == 8 ? max_blocks<T, 8>() : max_blocks<T, 16>();
 }
 
 template <typename T>
 cudaError_t launch_step3d(const CUtensorMap *maps_in, Fields<T> out, const RunDesc &run,
-                          unsigned *derr, int zchunks, int t3y, cudaStream_t s)
+                          unsigned *derr, int zchunks, int t3y, int sms, cudaStream_t s)
 {
-    if (t3y == 16) return launch<T, 16>(maps_in, out, run, derr, zchunks, s);
-    return launch<T, 8>(maps_in, out, run, derr, zchunks, s);
+    if (t3y == 8) return launch<T, 8>(maps_in, out, run, derr, zchunks, sms, s);
+    return launch<T, 16>(maps_in, out, run, derr, zchunks, sms, s);
 }
 
 template cudaError_t launch_step3d<float>(const CUtensorMap *, Fields<float>, const RunDesc &,
-                                          unsigned *, int, int, cudaStream_t);
+                                          unsigned *, int, int, int, cudaStream_t);
 template cudaError_t launch_step3d<double>(const CUtensorMap *, Fields<double>, const RunDesc &,
-                                           unsigned *, int, int, cudaStream_t);
+                                           unsigned *, int, int, int, cudaStream_t);
 template int step3d_max_blocks_per_sm<float>(int);
 template int step3d_max_blocks_per_sm<double>(int);
 
