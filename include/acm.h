@@ -167,6 +167,45 @@ acm_status acm_destroy(acm_handle *h);
  * (e.g. after a failed create).  Never NULL. */
 const char *acm_last_error(const acm_handle *h);
 
+/* ---- allocation-free diagnostics (the paper has no counterpart) ----------
+ * The same FP64 diagnostics as acm_reduce_mass, computed from fields the
+ * caller owns in device memory, for callers that cannot allocate device
+ * memory where they need them: code whose device memory belongs entirely to
+ * another runtime (a framework's caching allocator, a fixed pre-sized pool)
+ * and loops with a hard latency budget that forbid allocation after start-up.
+ * This call allocates nothing: no cudaMalloc, no cudaFree, no allocating
+ * library routine.  Its scratch (the block partials of the reduction and a
+ * run descriptor) lives in fixed file-scope device arrays inside libacm --
+ * room for the partials of at most 4096 blocks (256 KiB) -- that every GPU
+ * which loads the library holds until the process exits.
+ *
+ *   dim, nx, ny, nz  grid (nz = 1 in 2D); fields are contiguous [z][y][x],
+ *                    x fastest, unpadded
+ *   precision        ACM_FP64 (double arrays) or ACM_FP32_DEV (float arrays)
+ *   rho              ABSOLUTE density (device pointer)
+ *   u, v, w          velocity (device pointers; w ignored in 2D)
+ *   u_prev..w_prev   velocity before the last step for out[5], or all NULL
+ *                    (then out[5] = 0)
+ *   blocks           pass-1 blocks, 0 = default (min(ceil(n/256), 1024));
+ *                    more than 4096 is rejected with ACM_EINVAL
+ *   out_dev          DEVICE pointer to 8 doubles, same layout as one run of
+ *                    acm_reduce_mass; written asynchronously on STREAM
+ *   stream           cudaStream_t (NULL = legacy default stream)
+ * The first call on a device resolves the device addresses of the scratch
+ * arrays (cudaGetSymbolAddress, with that device current); make that first
+ * call before any stream capture.  Every call on a device shares the same
+ * scratch and keeps the last call's contents: each call rewrites every
+ * partial it later reads, so nothing needs clearing, but calls that overlap
+ * on the GPU (different streams, no ordering between them) race on it and
+ * must be serialised by the caller.  The call is asynchronous; errors found
+ * on the host return before anything is enqueued.  Message of the last
+ * failure on the calling thread: acm_noalloc_last_error(). */
+acm_status acm_reduce_mass_noalloc(int dim, int nx, int ny, int nz, int precision,
+                                   const void *rho, const void *u, const void *v, const void *w,
+                                   const void *u_prev, const void *v_prev, const void *w_prev,
+                                   int blocks, double *out_dev, void *stream);
+const char *acm_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

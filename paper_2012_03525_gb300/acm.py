@@ -20,7 +20,8 @@ TUNE_ZCHUNKS, TUNE_T3Y, TUNE_GRAPH_STEPS, TUNE_BLOCKS = 1, 2, 3, 4
 #: every symbol include/acm.h declares (checked by the CPU tests)
 EXPORTS = ["acm_create", "acm_batch_create", "acm_set_stream", "acm_nruns", "acm_set_fields",
            "acm_step", "acm_sync", "acm_fields", "acm_reduce_mass", "acm_set_tuning",
-           "acm_step_count", "acm_destroy", "acm_last_error"]
+           "acm_step_count", "acm_destroy", "acm_last_error", "acm_reduce_mass_noalloc",
+           "acm_noalloc_last_error"]
 
 
 class AcmError(RuntimeError):
@@ -70,6 +71,10 @@ def load():
         "acm_step_count": ([H], ctypes.c_int64),
         "acm_destroy": ([H], ctypes.c_int),
         "acm_last_error": ([H], ctypes.c_char_p),
+        "acm_reduce_mass_noalloc": ([ctypes.c_int] * 5 + [ctypes.c_void_p] * 7 +
+                                    [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p],
+                                    ctypes.c_int),
+        "acm_noalloc_last_error": ([], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -108,6 +113,19 @@ def _dptr(a):
         return ctypes.cast(ctypes.c_void_p(a), ctypes.POINTER(ctypes.c_double))
     assert a.dtype == np.float64 and a.flags.c_contiguous
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def reduce_mass_noalloc(dim, nx, ny, nz, precision, rho, u, v, w, prev, blocks, out_dev,
+                        stream=0):
+    """acm_reduce_mass_noalloc on caller-owned device buffers (raw device
+    addresses as ints; ``prev`` = (u_prev, v_prev, w_prev) addresses or None).
+    Raises AcmError on a non-zero status."""
+    lib = load()
+    pu, pv, pw = prev if prev is not None else (None, None, None)
+    st = lib.acm_reduce_mass_noalloc(dim, nx, ny, nz, precision, rho, u, v, w, pu, pv, pw,
+                                     blocks, out_dev, stream)
+    if st != OK:
+        raise AcmError(st, lib.acm_noalloc_last_error().decode())
 
 
 class Solver:
