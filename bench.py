@@ -188,6 +188,99 @@ def run_reference(args, rank, world):
     return 0
 
 
+def run_batched_drops(args):
+    """Batched two-phase drops (512 uneven 2D runs, FP32, one persistent launch
+    per step) against the plain scheme in FP64, one handle (and kernel launch
+    per step) per run; same steps, accuracy of the FP32 batch vs FP64."""
+    import numpy as np
+    import torch
+    from paper_2012_03525_gb300 import acm, build
+    from paper_2012_03525_gb300 import workloads as wl
+    build.build()
+    runs = wl.batch_drops(args.nruns)
+    params32, params64, states = [], [], []
+    for r in runs:
+        kw = dict(nu=r.nu, two_phase=True, sigma=r.sigma, W=r.W, M=r.M)
+        params32.append(acm.make_params((r.n, r.n), precision=acm.FP32_DEV, **kw))
+        params64.append(acm.make_params((r.n, r.n), precision=acm.FP64, **kw))
+        states.append(wl.drop2d(r.n, r.radius, r.W, eps=r.eps))
+    nodes = sum(r.n * r.n for r in runs)
+    stream = torch.cuda.Stream()
+    batch = acm.Solver(params32)
+    batch.set_stream(stream.cuda_stream)
+    for i, st in enumerate(states):
+        batch.set_fields(st[0], st[1], st[2], None, st[3], run=i)
+    tuned_ms = batch.autotune(10)
+    for i, st in enumerate(states):
+        batch.set_fields(st[0], st[1], st[2], None, st[3], run=i)
+    batch.step(max(args.warmup, 64))  # also captures the step graph
+    batch.sync()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        batch.step(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms32 = ev0.elapsed_time(ev1)
+    batch.sync()
+    red = batch.reduce()
+
+    # plain FP64 scheme: one handle per run, same number of steps
+    singles = []
+    for p, st in zip(params64, states):
+        h = acm.Solver(p)
+        h.set_fields(st[0], st[1], st[2], None, st[3])
+        singles.append(h)
+    for h in singles:
+        h.step(max(args.warmup, 64))  # also captures each handle's step graph
+    for h in singles:
+        h.sync()
+    t0 = time.perf_counter()
+    for h in singles:
+        h.step(args.steps)
+    for h in singles:
+        h.sync()
+    s64 = time.perf_counter() - t0
+    # accuracy of the FP32 batch against the FP64 runs (same initial state and steps)
+    errs_phi, errs_u = [], []
+    for i in range(0, len(runs), max(1, len(runs) // 16)):
+        g32 = batch.fields(run=i)
+        g64 = singles[i].fields()
+        errs_phi.append(float(np.linalg.norm(g32[4] - g64[4]) / np.linalg.norm(g64[4])))
+        den = max(np.linalg.norm(g64[1]), runs[i].sigma / runs[i].nu * math.sqrt(g64[1].size))
+        errs_u.append(float(np.linalg.norm(g32[1] - g64[1]) / den))
+    for h in singles:
+        h.close()
+    bytes_per_lu = 32  # rho', u, v, phi read and written, 4 B each
+    per_launch = ms32 / 1e3 / args.steps
+    peak, peak_kind = measured_peaks()
+    glups = nodes * args.steps / (ms32 / 1e3) / 1e9
+    print(json.dumps({
+        "metric": "GLUPS", "value": glups, "unit": "GLUPS", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms32 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"batched two-phase drops: {len(runs)} 2D runs, grids 64^2-512^2, "
+                               "seeded, FP32, one persistent launch per step",
+                   "nodes": nodes, "tuned_ms_per_step": tuned_ms,
+                   "blocks": batch.get_tuning(acm.TUNE_BLOCKS)},
+        "roofline": {"bound": "hbm", "achieved": bytes_per_lu * nodes / per_launch / 1e9,
+                     "peak": peak, "unit": "GB/s",
+                     "frac": bytes_per_lu * nodes / per_launch / 1e9 / peak,
+                     "peak_kind": f"{peak_kind} copy bandwidth", "traffic": None},
+        "gpu_launches": args.steps,
+        "plain_fp64_separate": {"seconds": s64, "GLUPS": nodes * args.steps / s64 / 1e9,
+                                "launches_per_step": len(runs),
+                                "speedup_of_batch": s64 / (ms32 / 1e3)},
+        "fp32_vs_fp64": {"phi_rel_l2_max": max(errs_phi), "u_rel_l2_max": max(errs_u),
+                         "sampled_runs": len(errs_phi)},
+        "mass_nonfinite": float(np.sum(red[:, 7])),
+        "clocks": clk.summary(),
+    }))
+    batch.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -195,6 +288,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="tgv3d", choices=["tgv3d", "drops"],
+                    help="tgv3d: the bench line; drops: the batched two-phase workload")
+    ap.add_argument("--nruns", type=int, default=512)
     ap.add_argument("--zchunks", type=int, default=env_int("ACM_ZCHUNKS", 0))
     ap.add_argument("--t3y", type=int, default=env_int("ACM_T3Y", 16))
     ap.add_argument("--n", type=int, default=N3,
@@ -208,6 +304,8 @@ def main():
 
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "drops":
+        return run_batched_drops(args)
 
     import numpy as np
     import torch

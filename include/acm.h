@@ -157,6 +157,17 @@ enum {
 };
 acm_status acm_set_tuning(acm_handle *h, int key, int value);
 
+/* Current value of a tuning knob (-1 for an unknown key or a NULL handle). */
+int acm_get_tuning(const acm_handle *h, int key);
+
+/* Autotuner: time NSTEPS steps of every candidate launch shape (3D: tile
+ * height x z-chunking; 2D: persistent CTA count) with CUDA events on the
+ * handle's stream, keep the fastest (readable with acm_get_tuning) and
+ * restore the fields as they were (trial steps run on a device copy, which
+ * this call allocates and frees).  *best_ms_per_step receives the winner's
+ * time per step.  Synchronous; needs acm_set_fields first. */
+acm_status acm_autotune(acm_handle *h, int nsteps, double *best_ms_per_step);
+
 /* Step counter since acm_set_fields. */
 int64_t acm_step_count(const acm_handle *h);
 

@@ -20,7 +20,8 @@ TUNE_ZCHUNKS, TUNE_T3Y, TUNE_GRAPH_STEPS, TUNE_BLOCKS = 1, 2, 3, 4
 #: every symbol include/acm.h declares (checked by the CPU tests)
 EXPORTS = ["acm_create", "acm_batch_create", "acm_set_stream", "acm_nruns", "acm_set_fields",
            "acm_step", "acm_sync", "acm_fields", "acm_reduce_mass", "acm_set_tuning",
-           "acm_step_count", "acm_destroy", "acm_last_error", "acm_reduce_mass_noalloc",
+           "acm_step_count", "acm_destroy", "acm_last_error", "acm_get_tuning", "acm_autotune",
+           "acm_reduce_mass_noalloc",
            "acm_noalloc_last_error"]
 
 
@@ -69,6 +70,8 @@ def load():
         "acm_reduce_mass": ([H, dp], ctypes.c_int),
         "acm_set_tuning": ([H, ctypes.c_int, ctypes.c_int], ctypes.c_int),
         "acm_step_count": ([H], ctypes.c_int64),
+        "acm_get_tuning": ([H, ctypes.c_int], ctypes.c_int),
+        "acm_autotune": ([H, ctypes.c_int, dp], ctypes.c_int),
         "acm_destroy": ([H], ctypes.c_int),
         "acm_last_error": ([H], ctypes.c_char_p),
         "acm_reduce_mass_noalloc": ([ctypes.c_int] * 5 + [ctypes.c_void_p] * 7 +
@@ -166,6 +169,16 @@ class Solver:
 
     def set_tuning(self, key: int, value: int):
         self._check(self._lib.acm_set_tuning(self._h, key, value))
+
+    def get_tuning(self, key: int) -> int:
+        return self._lib.acm_get_tuning(self._h, key)
+
+    def autotune(self, nsteps: int = 20) -> float:
+        """Pick the fastest launch shape (fields are left unchanged); returns
+        the winner's milliseconds per step."""
+        ms = ctypes.c_double(0.0)
+        self._check(self._lib.acm_autotune(self._h, int(nsteps), ctypes.byref(ms)))
+        return ms.value
 
     def set_fields(self, rho, u, v, w=None, phi=None, run=0):
         self._check(self._lib.acm_set_fields(self._h, run, _dptr(rho), _dptr(u), _dptr(v),

@@ -469,6 +469,128 @@ acm_status acm_set_tuning(acm_handle *h, int key, int value)
     return ACM_OK;
 }
 
+int acm_get_tuning(const acm_handle *h, int key)
+{
+    if (!h) return -1;
+    switch (key) {
+    case ACM_TUNE_ZCHUNKS: return h->tune.zchunks;
+    case ACM_TUNE_T3Y: return h->tune.t3y;
+    case ACM_TUNE_GRAPH_STEPS: return h->tune.graph_steps;
+    case ACM_TUNE_BLOCKS: return h->tune.blocks;
+    default: return -1;
+    }
+}
+
+acm_status acm_autotune(acm_handle *h, int nsteps, double *best_ms_per_step)
+{
+    if (!h) return fail(nullptr, ACM_EINVAL, "null handle");
+    if (nsteps < 1) return fail(h, ACM_EINVAL, "nsteps must be >= 1");
+    for (int r = 0; r < h->nruns; ++r)
+        if (!h->have_fields[r]) return fail(h, ACM_ESTATE, "acm_set_fields not called for every run");
+    if (h->sticky) return fail(h, ACM_EUNSTABLE, "fields already non-finite");
+    CK(h, cudaSetDevice(h->device));
+    CK(h, cudaStreamSynchronize(h->stream));
+
+    // candidate launch shapes
+    struct Cand { int t3y, zchunks, blocks; };
+    std::vector<Cand> cands;
+    if (h->dim == 3) {
+        const int nz = h->runs[0].nz;
+        const int zc_opts[4] = {0, std::max(1, nz / 8), std::max(1, nz / 32), std::max(1, nz / 64)};
+        for (int t3y : {16, 8})
+            for (int zc : zc_opts) {
+                bool dup = false;
+                for (const Cand &c : cands) dup |= (c.t3y == t3y && c.zchunks == zc);
+                if (!dup) cands.push_back({t3y, zc, 0});
+            }
+    } else {
+        const int per_sm = h->prec == ACM_FP64 ? step2d_max_blocks_per_sm<double>(h->two_phase)
+                                               : step2d_max_blocks_per_sm<float>(h->two_phase);
+        for (int k = 1; k <= per_sm; ++k) cands.push_back({h->tune.t3y, 0, k * h->sms});
+    }
+
+    // keep the state: trial steps run on a copy
+    const size_t bytes = h->pool * h->esize();
+    void *save[NFIELD] = {};
+    acm_status st = ACM_OK;
+    for (int f = 0; f < NFIELD && st == ACM_OK; ++f) {
+        if (!field_used(h, f)) continue;
+        cudaError_t e = cudaMalloc(&save[f], bytes);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(save[f], h->buf[h->cur][f], bytes, cudaMemcpyDeviceToDevice,
+                                h->stream);
+        if (e != cudaSuccess) st = cuda_fail(h, e, "autotune state copy");
+    }
+    const int cur0 = h->cur;
+    const Tuning keep = h->tune;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    double best = 1e300;
+    Cand bestc = {keep.t3y, keep.zchunks, keep.blocks};
+    if (st == ACM_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+        st = fail(h, ACM_ECUDA, "cudaEventCreate failed");
+    for (size_t i = 0; i < cands.size() && st == ACM_OK; ++i) {
+        const Cand &c = cands[i];
+        if (h->dim == 3 && c.t3y != h->tune.t3y) {
+            h->tune.t3y = c.t3y;
+            if (build_maps(h) != ACM_OK) {
+                st = ACM_ECUDA;
+                break;
+            }
+        }
+        h->tune.zchunks = c.zchunks;
+        h->tune.blocks = c.blocks;
+        cudaError_t e = cudaSuccess;
+        for (int k = 0; k < 2 && e == cudaSuccess; ++k) {  // warm-up
+            e = step_once(h, h->cur);
+            h->cur ^= 1;
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+        for (int k = 0; k < nsteps && e == cudaSuccess; ++k) {
+            e = step_once(h, h->cur);
+            h->cur ^= 1;
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            st = cuda_fail(h, e, "autotune trial");
+            break;
+        }
+        if (ms / nsteps < best) {
+            best = ms / nsteps;
+            bestc = c;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    // restore the state and apply the winner
+    h->cur = cur0;
+    for (int f = 0; f < NFIELD; ++f) {
+        if (!save[f]) continue;
+        if (st == ACM_OK) {
+            cudaError_t e = cudaMemcpyAsync(h->buf[cur0][f], save[f], bytes,
+                                            cudaMemcpyDeviceToDevice, h->stream);
+            if (e != cudaSuccess) st = cuda_fail(h, e, "autotune restore");
+        }
+    }
+    cudaStreamSynchronize(h->stream);
+    for (int f = 0; f < NFIELD; ++f)
+        if (save[f]) cudaFree(save[f]);
+    h->tune = keep;
+    if (st == ACM_OK) {
+        h->tune.zchunks = bestc.zchunks;
+        h->tune.blocks = bestc.blocks;
+        if (h->dim == 3) h->tune.t3y = bestc.t3y;
+    }
+    if (h->dim == 3 && build_maps(h) != ACM_OK && st == ACM_OK) st = ACM_ECUDA;
+    drop_graph(h);
+    cudaMemsetAsync(h->derr, 0, sizeof(unsigned), h->stream);
+    cudaStreamSynchronize(h->stream);
+    if (best_ms_per_step) *best_ms_per_step = st == ACM_OK ? best : 0.0;
+    return st;
+}
+
 acm_status acm_set_fields(acm_handle *h, int run, const double *rho, const double *u,
                           const double *v, const double *w, const double *phi)
 {

@@ -361,3 +361,60 @@ def test_graph_and_direct_launch_bitwise_equal():
             out.append(s.fields())
     for a, b in zip(out[0][:4], out[1][:4]):
         assert np.array_equal(a, b)
+
+
+# ------------------------------------------------------------------- autotuner
+@pytest.mark.parametrize("shape,prec", [((40, 36, 64), acm.FP32_DEV), ((70, 90), acm.FP64)])
+def test_autotune_keeps_state_and_results(oracle_lib, shape, prec):
+    """The autotuner times trial steps on a copy: the fields are unchanged
+    afterwards and the tuned launch shape gives the same answer."""
+    rng = np.random.default_rng(8)
+    st = [1 + 0.01 * _smooth(rng, shape)] + [0.03 * _smooth(rng, shape) for _ in shape]
+    out = []
+    for tune in (False, True):
+        with acm.Solver(acm.make_params(shape, nu=0.05, precision=prec)) as s:
+            s.set_fields(*st)
+            before = s.fields()
+            if tune:
+                ms = s.autotune(4)
+                assert ms > 0
+                after = s.fields()
+                for a, b in zip(before[:4], after[:4]):
+                    if a is not None:
+                        assert np.array_equal(a, b)
+            s.step(25)
+            out.append(s.fields())
+    tol = 1e-13 if prec == acm.FP64 else 1e-6
+    for a, b in zip(out[0][:4], out[1][:4]):
+        if a is not None:
+            assert rel_l2(b - (1.0 if a is out[0][0] else 0.0),
+                          a - (1.0 if a is out[0][0] else 0.0)) < tol
+
+
+def test_batched_laplace_law_small_drops():
+    """A batch of small static drops relaxes to mu0 = sigma / (2R) (Laplace
+    law through the Gibbs-Thomson relation): the radius is measured from the
+    drop area, mu from phi with the Section 2 formula on the host."""
+    sig, W, M = 3e-2, 4.0, 1.0
+    runs = [(48, 12.0), (40, 10.0), (56, 14.0)]
+    params = [acm.make_params((n, n), nu=0.1, two_phase=True, sigma=sig, W=W, M=M)
+              for n, _ in runs]
+    with acm.Solver(params) as s:
+        for i, (n, R) in enumerate(runs):
+            st = wl.drop2d(n, R, W)
+            s.set_fields(st[0], st[1], st[2], None, st[3], run=i)
+        s.step(8000)
+        for i, (n, R) in enumerate(runs):
+            phi = s.fields(run=i)[4]
+            a, kappa = 3 * sig / (4 * W), 3 * sig * W / 8
+            # D2Q9 Laplacian of phi, periodic
+            def sh(f, dy, dx):
+                return np.roll(np.roll(f, -dy, 0), -dx, 1)
+            lap = (2 / 3) * (sh(phi, 0, 1) + sh(phi, 0, -1) + sh(phi, 1, 0) + sh(phi, -1, 0) - 4 * phi) \
+                + (1 / 6) * (sh(phi, 1, 1) + sh(phi, 1, -1) + sh(phi, -1, 1) + sh(phi, -1, -1) - 4 * phi)
+            mu = 4 * a * phi * (phi ** 2 - 1) - kappa * lap
+            r_eff = math.sqrt(((1 + phi) / 2).sum() / math.pi)
+            c = (n - 1) / 2
+            X, Y = np.meshgrid(np.arange(n), np.arange(n))
+            core = np.hypot(X - c, Y - c) < r_eff / 2
+            assert mu[core].mean() == pytest.approx(sig / (2 * r_eff), rel=0.1)
