@@ -178,6 +178,48 @@ acm_status acm_destroy(acm_handle *h);
  * (e.g. after a failed create).  Never NULL. */
 const char *acm_last_error(const acm_handle *h);
 
+/* ---- learned closure ------------------------------------------------------
+ * A small convolutional network that corrects a coarse-grid state after
+ * solver steps: three periodic 3x3 convolutions, channels 3 -> 32 -> 32 -> 3,
+ * ReLU after the first two; its output is added to the normalised state
+ * (rho' s_rho, u s_u, v s_u).  BF16 weights and activations on the tensor
+ * cores, FP32 accumulation, FP32 master weights trained with Adam.  This is
+ * an addition to the method of the paper (a learned correction of the coarse
+ * scheme); the scheme itself stays the judge of its error.
+ *
+ * Normalised state tensors are FP32 [batch][3][ny][nx] in device memory
+ * (channel 0 = s_rho rho', 1 = s_u u, 2 = s_u v).  Weights are a flat FP32
+ * vector: for each layer W[cout][cin][3][3] then b[cout]. */
+typedef struct acm_closure acm_closure;
+
+/* number of weights and biases (11011) */
+size_t acm_closure_num_params(void);
+/* grid nx x ny (nx a multiple of 16, ny of 8), BATCH states per call */
+acm_status acm_closure_create(int nx, int ny, int batch, acm_closure **out);
+acm_status acm_closure_set_stream(acm_closure *c, void *stream);
+/* normalisation scales s_rho, s_u, s_u (s_u shared by u and v) */
+acm_status acm_closure_set_scales(acm_closure *c, const float *scales3);
+/* host FP32 weights in, resets the Adam state; or weights out */
+acm_status acm_closure_set_weights(acm_closure *c, const float *w, size_t n);
+acm_status acm_closure_get_weights(acm_closure *c, float *w, size_t n);
+/* net(x) for normalised x -> net_dev (same layout), asynchronous */
+acm_status acm_closure_forward(acm_closure *c, const float *x_dev, float *net_dev);
+/* loss = mean((x + net(x) - target)^2) and its gradient (grad_host may be
+ * NULL; n = acm_closure_num_params()); synchronous */
+acm_status acm_closure_loss_grad(acm_closure *c, const float *x_dev, const float *target_dev,
+                                 double *loss, float *grad_host);
+/* one Adam step (beta 0.9/0.999, eps 1e-8) on that loss; *loss = the loss
+ * before the step (loss may be NULL: then the step stays asynchronous) */
+acm_status acm_closure_train_step(acm_closure *c, const float *x_dev, const float *target_dev,
+                                  float lr, double *loss);
+/* normalised state of runs 0..batch-1 of an FP32 2D handle -> x_dev */
+acm_status acm_closure_gather(acm_closure *c, acm_handle *h, float *x_dev);
+/* correct runs 0..batch-1 of the handle in place: state += net(state)/scale.
+ * Waits for the handle's stream before and for the closure's stream after. */
+acm_status acm_closure_apply(acm_closure *c, acm_handle *h);
+acm_status acm_closure_destroy(acm_closure *c);
+const char *acm_closure_last_error(const acm_closure *c);
+
 /* ---- allocation-free diagnostics (the paper has no counterpart) ----------
  * The same FP64 diagnostics as acm_reduce_mass, computed from fields the
  * caller owns in device memory, for callers that cannot allocate device

@@ -84,18 +84,22 @@ def forward(params, x, bf16_activations=False):
     return out, (h1, h2)
 
 
-def loss_and_grads(params, x, target, bf16_activations=False):
+def loss_and_grads(params, x, target, bf16_activations=False, bf16_grads=False):
     """MSE loss mean((x + net(x) - target)^2) over all elements and the
-    gradients of every weight and bias (x is not differentiated)."""
+    gradients of every weight and bias (x is not differentiated).
+    ``bf16_grads`` rounds the stored activation gradients (d loss / d out and
+    the masked hidden-layer gradients) to bfloat16 where the kernels store
+    them."""
+    qg = to_bf16 if bf16_grads else (lambda a: a)
     out, (h1, h2) = forward(params, x, bf16_activations)
     r = x + out - target
     n = r.size
     loss = float((r * r).sum() / n)
-    d3 = 2.0 * r / n
+    d3 = qg(2.0 * r / n)
     dh2, dW3, db3 = conv3x3_grad(h2, params[2][0], d3)
-    dh2 = dh2 * (h2 > 0)
+    dh2 = qg(dh2 * (h2 > 0))
     dh1, dW2, db2 = conv3x3_grad(h1, params[1][0], dh2)
-    dh1 = dh1 * (h1 > 0)
+    dh1 = qg(dh1 * (h1 > 0))
     _, dW1, db1 = conv3x3_grad(x, params[0][0], dh1)
     return loss, [(dW1, db1), (dW2, db2), (dW3, db3)]
 

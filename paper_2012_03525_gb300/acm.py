@@ -21,7 +21,11 @@ TUNE_ZCHUNKS, TUNE_T3Y, TUNE_GRAPH_STEPS, TUNE_BLOCKS = 1, 2, 3, 4
 EXPORTS = ["acm_create", "acm_batch_create", "acm_set_stream", "acm_nruns", "acm_set_fields",
            "acm_step", "acm_sync", "acm_fields", "acm_reduce_mass", "acm_set_tuning",
            "acm_step_count", "acm_destroy", "acm_last_error", "acm_get_tuning", "acm_autotune",
-           "acm_reduce_mass_noalloc",
+           "acm_closure_num_params", "acm_closure_create", "acm_closure_set_stream",
+           "acm_closure_set_scales", "acm_closure_set_weights", "acm_closure_get_weights",
+           "acm_closure_forward", "acm_closure_loss_grad", "acm_closure_train_step",
+           "acm_closure_gather", "acm_closure_apply", "acm_closure_destroy",
+           "acm_closure_last_error", "acm_reduce_mass_noalloc",
            "acm_noalloc_last_error"]
 
 
@@ -78,6 +82,24 @@ def load():
                                     [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p],
                                     ctypes.c_int),
         "acm_noalloc_last_error": ([], ctypes.c_char_p),
+        "acm_closure_num_params": ([], ctypes.c_size_t),
+        "acm_closure_create": ([ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+        "acm_closure_set_stream": ([H, ctypes.c_void_p], ctypes.c_int),
+        "acm_closure_set_scales": ([H, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
+        "acm_closure_set_weights": ([H, ctypes.POINTER(ctypes.c_float), ctypes.c_size_t],
+                                    ctypes.c_int),
+        "acm_closure_get_weights": ([H, ctypes.POINTER(ctypes.c_float), ctypes.c_size_t],
+                                    ctypes.c_int),
+        "acm_closure_forward": ([H, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+        "acm_closure_loss_grad": ([H, ctypes.c_void_p, ctypes.c_void_p, dp,
+                                   ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
+        "acm_closure_train_step": ([H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float, dp],
+                                   ctypes.c_int),
+        "acm_closure_gather": ([H, H, ctypes.c_void_p], ctypes.c_int),
+        "acm_closure_apply": ([H, H], ctypes.c_int),
+        "acm_closure_destroy": ([H], ctypes.c_int),
+        "acm_closure_last_error": ([H], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -223,6 +245,85 @@ class Solver:
         if self._h:
             self._lib.acm_destroy(self._h)
             self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Closure:
+    """The learned closure (acm_closure_*): device tensors are passed as raw
+    device addresses (ints), host weight vectors as NumPy float32 arrays."""
+
+    def __init__(self, nx, ny, batch):
+        lib = load()
+        self._lib = lib
+        self._c = ctypes.c_void_p()
+        st = lib.acm_closure_create(nx, ny, batch, ctypes.byref(self._c))
+        if st != OK:
+            raise AcmError(st, lib.acm_closure_last_error(None).decode())
+        self.nx, self.ny, self.batch = nx, ny, batch
+        self.nparams = lib.acm_closure_num_params()
+
+    def _check(self, st):
+        if st != OK:
+            raise AcmError(st, self._lib.acm_closure_last_error(self._c).decode())
+
+    def set_stream(self, stream_ptr):
+        self._check(self._lib.acm_closure_set_stream(self._c, ctypes.c_void_p(stream_ptr)))
+
+    def set_scales(self, s_rho, s_u):
+        arr = (ctypes.c_float * 3)(s_rho, s_u, s_u)
+        self._check(self._lib.acm_closure_set_scales(self._c, arr))
+
+    def set_weights(self, w):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        self._check(self._lib.acm_closure_set_weights(
+            self._c, w.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), w.size))
+
+    def get_weights(self):
+        w = np.empty(self.nparams, dtype=np.float32)
+        self._check(self._lib.acm_closure_get_weights(
+            self._c, w.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), w.size))
+        return w
+
+    def forward(self, x_dev, net_dev):
+        self._check(self._lib.acm_closure_forward(self._c, ctypes.c_void_p(x_dev),
+                                                  ctypes.c_void_p(net_dev)))
+
+    def loss_grad(self, x_dev, target_dev):
+        loss = ctypes.c_double(0.0)
+        g = np.empty(self.nparams, dtype=np.float32)
+        self._check(self._lib.acm_closure_loss_grad(
+            self._c, ctypes.c_void_p(x_dev), ctypes.c_void_p(target_dev), ctypes.byref(loss),
+            g.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return loss.value, g
+
+    def train_step(self, x_dev, target_dev, lr, want_loss=True):
+        loss = ctypes.c_double(0.0)
+        self._check(self._lib.acm_closure_train_step(
+            self._c, ctypes.c_void_p(x_dev), ctypes.c_void_p(target_dev), ctypes.c_float(lr),
+            ctypes.byref(loss) if want_loss else None))
+        return loss.value if want_loss else None
+
+    def gather(self, solver, x_dev):
+        self._check(self._lib.acm_closure_gather(self._c, solver._h, ctypes.c_void_p(x_dev)))
+
+    def apply(self, solver):
+        self._check(self._lib.acm_closure_apply(self._c, solver._h))
+
+    def close(self):
+        if self._c:
+            self._lib.acm_closure_destroy(self._c)
+            self._c = ctypes.c_void_p()
 
     def __enter__(self):
         return self

@@ -408,6 +408,22 @@ acm_status check_flags(acm_handle *h)
 
 }  // namespace
 
+namespace acm {
+acm_status handle_fields_f32(acm_handle *h, int run, float **r, float **u, float **v, int *nx,
+                             int *ny)
+{
+    if (!h || run < 0 || run >= h->nruns || h->dim != 2 || h->prec != ACM_FP32_DEV)
+        return ACM_EINVAL;
+    const RunDesc &R = h->runs[run];
+    *r = static_cast<float *>(h->buf[h->cur][F_R]) + R.off;
+    *u = static_cast<float *>(h->buf[h->cur][F_U]) + R.off;
+    *v = static_cast<float *>(h->buf[h->cur][F_V]) + R.off;
+    *nx = R.nx;
+    *ny = R.ny;
+    return ACM_OK;
+}
+}  // namespace acm
+
 extern "C" {
 
 acm_status acm_create(const acm_params *params, acm_handle **out)

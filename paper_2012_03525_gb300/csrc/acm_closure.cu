@@ -1,0 +1,718 @@
+// Learned closure: a 3-layer 3x3 convolutional network (3 -> 32 -> 32 -> 3,
+// ReLU after the first two layers) that corrects a coarse-grid state
+// (rho', u, v) after solver steps, with its training on the GPU.
+//
+// All convolutions are periodic 2D cross-correlations run on the tensor
+// cores (mma.sync m16n8k16, BF16 operands, FP32 accumulation):
+//   * forward:        Y[co, p] = sum_K A[co, K] X[K, p], K = (tap, ci),
+//                     A = W in [co][tap][ci] order, X = shifted input pixels;
+//   * data gradient:  dX = (W flipped, channels swapped) applied to dY -- the
+//                     same kernel with a rearranged weight matrix;
+//   * weight gradient: dW[co, (tap, ci)] = sum_p dY[co, p] X[p + off(tap), ci]
+//                     -- a GEMM whose reduction runs over pixels; per-CTA
+//                     partials are summed in a fixed order (deterministic).
+// Activations and gradients are stored as BF16 NHWC (channels contiguous),
+// the master weights, Adam moments, losses and corrections in FP32.
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "acm_internal.h"
+
+namespace acm {
+namespace {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int CTH = 8, CTW = 16, CTP = CTH * CTW;  // pixel tile
+constexpr int CTHREADS = 256;                     // 8 warps, warp w = tile row w
+constexpr int HALO = (CTH + 2) * (CTW + 2);
+
+// real / padded channel counts of the three layers
+constexpr int NL = 3;
+constexpr int CIN[NL] = {3, 32, 32}, COUT[NL] = {32, 32, 3};
+constexpr int CINP[NL] = {16, 32, 32}, COUTP[NL] = {32, 32, 16};
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4],
+                                         const uint32_t (&b)[2])
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ uint32_t ld32(const bf16 *p)
+{
+    return *reinterpret_cast<const uint32_t *>(p);
+}
+
+__device__ __forceinline__ int wrapi(int c, int n)
+{
+    c %= n;
+    return c < 0 ? c + n : c;
+}
+
+enum { OUT_RELU_BF16 = 0, OUT_MASK_BF16 = 1, OUT_F32_NCHW = 2 };
+
+// One 3x3 convolution layer (or its data gradient) on an 8 x 16 pixel tile.
+// x: [B][H][W][CI] bf16; A: [CO][9*CI] bf16; output by MODE (see above).
+template <int CI, int CO, int MODE>
+__global__ void __launch_bounds__(CTHREADS)
+    k_conv(const bf16 *__restrict__ x, const bf16 *__restrict__ A, const float *__restrict__ bias,
+           const bf16 *__restrict__ mask, void *__restrict__ out, int H, int W, int nout)
+{
+    constexpr int XST = CI + 8;          // smem pixel stride (bank-conflict free)
+    constexpr int K = 9 * CI, AST = K + 8;
+    constexpr int MT = CO / 16;
+    __shared__ __align__(16) bf16 xs[HALO * XST];
+    __shared__ __align__(16) bf16 as[CO * AST];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    const int x0 = blockIdx.x * CTW, y0 = blockIdx.y * CTH, img = blockIdx.z;
+    const bf16 *xi = x + (size_t)img * H * W * CI;
+
+    // weights: CO rows of K bf16 (16-byte chunks)
+    for (int i = tid; i < CO * (K / 8); i += CTHREADS) {
+        const int r = i / (K / 8), c = i - r * (K / 8);
+        *reinterpret_cast<uint4 *>(&as[r * AST + c * 8]) =
+            *reinterpret_cast<const uint4 *>(&A[(size_t)r * K + c * 8]);
+    }
+    // input tile with a one-pixel periodic halo
+    for (int i = tid; i < HALO * (CI / 8); i += CTHREADS) {
+        const int hp = i / (CI / 8), c = i - hp * (CI / 8);
+        const int hy = hp / (CTW + 2), hx = hp - hy * (CTW + 2);
+        const int gy = wrapi(y0 - 1 + hy, H), gx = wrapi(x0 - 1 + hx, W);
+        *reinterpret_cast<uint4 *>(&xs[hp * XST + c * 8]) =
+            *reinterpret_cast<const uint4 *>(&xi[((size_t)gy * W + gx) * CI + c * 8]);
+    }
+    __syncthreads();
+
+    float acc[MT][2][4];
+#pragma unroll
+    for (int m = 0; m < MT; ++m)
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[m][j][e] = 0.f;
+
+#pragma unroll 1
+    for (int tap = 0; tap < 9; ++tap) {
+        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+#pragma unroll
+        for (int cb = 0; cb < CI / 16; ++cb) {
+            const int k0 = tap * CI + cb * 16;
+            uint32_t a[MT][4];
+#pragma unroll
+            for (int m = 0; m < MT; ++m) {
+                const bf16 *ap = &as[(m * 16 + g) * AST + k0 + 2 * t];
+                a[m][0] = ld32(ap);
+                a[m][1] = ld32(ap + 8 * AST);
+                a[m][2] = ld32(ap + 8);
+                a[m][3] = ld32(ap + 8 * AST + 8);
+            }
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int hp = (w + 1 + dy) * (CTW + 2) + (8 * j + g + 1 + dx);
+                const bf16 *bp = &xs[hp * XST + cb * 16 + 2 * t];
+                const uint32_t b[2] = {ld32(bp), ld32(bp + 8)};
+#pragma unroll
+                for (int m = 0; m < MT; ++m) mma_bf16(acc[m][j], a[m], b);
+            }
+        }
+    }
+
+    // epilogue: element e of a fragment is (co = 16m + g + 8 (e >> 1), px = 8j + 2t + (e & 1))
+#pragma unroll
+    for (int m = 0; m < MT; ++m)
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int co = m * 16 + g + 8 * (e >> 1);
+                const int px = x0 + 8 * j + 2 * t + (e & 1), py = y0 + w;
+                const size_t pix = (size_t)img * H * W + (size_t)py * W + px;
+                float vv = acc[m][j][e];
+                if (MODE == OUT_RELU_BF16) {
+                    vv = fmaxf(vv + bias[co], 0.f);
+                    static_cast<bf16 *>(out)[pix * CO + co] = __float2bfloat16_rn(vv);
+                } else if (MODE == OUT_MASK_BF16) {
+                    const float mk = __bfloat162float(mask[pix * CO + co]);
+                    static_cast<bf16 *>(out)[pix * CO + co] =
+                        __float2bfloat16_rn(mk > 0.f ? vv : 0.f);
+                } else {
+                    if (co < nout)
+                        static_cast<float *>(out)[((size_t)img * nout + co) * H * W +
+                                                  (size_t)py * W + px] = vv + bias[co];
+                }
+            }
+}
+
+// Weight-gradient partials: every CTA reduces `tiles` pixel tiles of one image
+// into D[co][(tap, ci)] (and the bias gradient) and writes its partial.
+// dy: [B][H][W][CO] bf16, x: [B][H][W][CI] bf16.
+template <int CI, int CO>
+__global__ void __launch_bounds__(CTHREADS)
+    k_wgrad(const bf16 *__restrict__ dy, const bf16 *__restrict__ x, float *__restrict__ partial,
+            int H, int W, int tiles_per_cta)
+{
+    constexpr int N = 9 * CI, MT = CO / 16, NT = N / 8;
+    constexpr int NTW = (NT + 7) / 8;     // n-tiles per warp (round robin)
+    constexpr int DST = CTP + 8;          // dyT row stride (co rows, pixels contiguous)
+    constexpr int XR = CTW + 8;           // xS row stride (>= CTW + 2)
+    constexpr int XCH = (CTH + 2) * XR + 8;  // xS channel stride
+    __shared__ __align__(16) bf16 dyT[CO * DST];
+    // X tile with its halo rows, transposed to [ci][r][c], in two copies so the
+    // pixel pair (2t, 2t+1) of a B fragment is one aligned 32-bit word for
+    // every dx: copy 0 starts at column x0-1 (used for dx = -1, +1), copy 1 at
+    // column x0 (used for dx = 0)
+    __shared__ __align__(16) bf16 xS[2 * CI * XCH];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    const int tiles_x = W / CTW, tiles_img = tiles_x * (H / CTH);
+    const int img = blockIdx.y;
+    const bf16 *dyi = dy + (size_t)img * H * W * CO;
+    const bf16 *xi = x + (size_t)img * H * W * CI;
+
+    float acc[MT][NTW][4];
+#pragma unroll
+    for (int m = 0; m < MT; ++m)
+#pragma unroll
+        for (int q = 0; q < NTW; ++q)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[m][q][e] = 0.f;
+    float bacc = 0.f;  // thread co < CO: bias-gradient running sum
+
+    for (int k = 0; k < tiles_per_cta; ++k) {
+        const int tile = blockIdx.x * tiles_per_cta + k;
+        if (tile >= tiles_img) break;
+        const int x0 = (tile % tiles_x) * CTW, y0 = (tile / tiles_x) * CTH;
+        __syncthreads();
+        // dY tile transposed: dyT[co][p], p = 16 r + c
+        for (int i = tid; i < CTP * CO; i += CTHREADS) {
+            const int p = i / CO, co = i - p * CO;
+            const int py = y0 + p / CTW, px = x0 + p % CTW;
+            dyT[co * DST + p] = dyi[((size_t)py * W + px) * CO + co];
+        }
+        for (int i = tid; i < (CTH + 2) * (CTW + 2) * CI; i += CTHREADS) {
+            const int hp = i / CI, ci = i - hp * CI;
+            const int r = hp / (CTW + 2), hc = hp - r * (CTW + 2);  // column x0 - 1 + hc
+            const bf16 val = xi[((size_t)wrapi(y0 - 1 + r, H) * W + wrapi(x0 - 1 + hc, W)) * CI + ci];
+            xS[ci * XCH + r * XR + hc] = val;
+            if (hc >= 1 && hc <= CTW) xS[(CI + ci) * XCH + r * XR + hc - 1] = val;
+        }
+        __syncthreads();
+        if (tid < CO) {
+            float s = 0.f;
+            for (int p = 0; p < CTP; ++p) s += __bfloat162float(dyT[tid * DST + p]);
+            bacc += s;
+        }
+        // K loop: one k16 block = one tile row (16 pixels)
+#pragma unroll 1
+        for (int row = 0; row < CTH; ++row) {
+            uint32_t a[MT][4];
+#pragma unroll
+            for (int m = 0; m < MT; ++m) {
+                const bf16 *ap = &dyT[(m * 16 + g) * DST + row * CTW + 2 * t];
+                a[m][0] = ld32(ap);
+                a[m][1] = ld32(ap + 8 * DST);
+                a[m][2] = ld32(ap + 8);
+                a[m][3] = ld32(ap + 8 * DST + 8);
+            }
+#pragma unroll
+            for (int q = 0; q < NTW; ++q) {
+                const int nt = w + 8 * q;
+                if (nt < NT) {
+                    const int n = nt * 8 + g;            // column (tap, ci)
+                    const int tap = n / CI, ci = n - tap * CI;
+                    const int dyy = tap / 3 - 1, dx = tap % 3 - 1;
+                    // pixel column 2t + dx of the row: copy 1 at 2t (dx = 0),
+                    // copy 0 at 2t + 1 + dx (dx = -1 or +1, even)
+                    const bf16 *bp = dx == 0
+                        ? &xS[(CI + ci) * XCH + (row + 1 + dyy) * XR + 2 * t]
+                        : &xS[ci * XCH + (row + 1 + dyy) * XR + 2 * t + 1 + dx];
+                    const uint32_t b[2] = {ld32(bp), ld32(bp + 8)};
+#pragma unroll
+                    for (int m = 0; m < MT; ++m) mma_bf16(acc[m][q], a[m], b);
+                }
+            }
+        }
+    }
+    // write the partial: [CO][N] then the bias partial [CO]
+    float *dst = partial + ((size_t)img * gridDim.x + blockIdx.x) * (CO * N + CO);
+#pragma unroll
+    for (int m = 0; m < MT; ++m)
+#pragma unroll
+        for (int q = 0; q < NTW; ++q) {
+            const int nt = w + 8 * q;
+            if (nt < NT)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int co = m * 16 + g + 8 * (e >> 1);
+                    const int n = nt * 8 + 2 * t + (e & 1);
+                    dst[co * N + n] = acc[m][q][e];
+                }
+        }
+    if (tid < CO) dst[CO * N + tid] = bacc;
+}
+
+// Sum the partials in a fixed order and scatter into the master layout
+// (per layer W[co][ci][3][3] then b[co]; padded channels dropped).
+__global__ void k_wgrad_sum(const float *__restrict__ partial, int nparts, int cin, int cout,
+                            int cinp, int coutp, float *__restrict__ grad)
+{
+    const int N = 9 * cinp, stride = coutp * N + coutp;
+    const int total = cout * cin * 9 + cout;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < total; j += gridDim.x * blockDim.x) {
+        int src;
+        if (j < cout * cin * 9) {
+            const int co = j / (cin * 9), rem = j - co * cin * 9, ci = rem / 9, tap = rem % 9;
+            src = co * N + tap * cinp + ci;
+        } else {
+            src = coutp * N + (j - cout * cin * 9);
+        }
+        float s = 0.f;
+        for (int b = 0; b < nparts; ++b) s += partial[(size_t)b * stride + src];
+        grad[j] = s;
+    }
+}
+
+// master FP32 weights -> forward matrices A_l [COUTP][9][CINP] and the
+// data-gradient matrices B_l [CINP][9][COUTP] with B[ci][t][co] = W[co][ci][8 - t]
+__global__ void k_prep_weights(const float *__restrict__ master, bf16 *A0, bf16 *A1, bf16 *A2,
+                               bf16 *B1, bf16 *B2, float *b0, float *b1, float *b2)
+{
+    bf16 *As[NL] = {A0, A1, A2};
+    bf16 *Bs[NL] = {nullptr, B1, B2};
+    float *bs[NL] = {b0, b1, b2};
+    const int cins[NL] = {3, 32, 32}, couts[NL] = {32, 32, 3};
+    const int cinps[NL] = {16, 32, 32}, coutps[NL] = {32, 32, 16};
+    int off = 0;
+    for (int l = 0; l < NL; ++l) {
+        const int cin = cins[l], cout = couts[l], cinp = cinps[l], coutp = coutps[l];
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < coutp * 9 * cinp;
+             i += gridDim.x * blockDim.x) {
+            const int co = i / (9 * cinp), rem = i - co * 9 * cinp, tap = rem / cinp,
+                      ci = rem - tap * cinp;
+            const float v = (co < cout && ci < cin) ? master[off + (co * cin + ci) * 9 + tap] : 0.f;
+            As[l][i] = __float2bfloat16_rn(v);
+            if (Bs[l]) {
+                // element (co, tap, ci) of W feeds B[ci][8 - tap][co]
+                Bs[l][(ci * 9 + (8 - tap)) * coutp + co] = __float2bfloat16_rn(v);
+            }
+        }
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < coutp; i += gridDim.x * blockDim.x)
+            bs[l][i] = i < cout ? master[off + cout * cin * 9 + i] : 0.f;
+        off += cout * cin * 9 + cout;
+    }
+}
+
+// normalised FP32 NCHW state (3 channels) -> BF16 NHWC with 16 channels
+__global__ void k_pack_nhwc(const float *__restrict__ xin, bf16 *__restrict__ x16, int HW,
+                            int batch)
+{
+    const long long n = (long long)batch * HW;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long img = i / HW, p = i - img * HW;
+        __align__(16) bf16 v[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c)
+            v[c] = __float2bfloat16_rn(c < 3 ? xin[(img * 3 + c) * HW + p] : 0.f);
+        uint4 *d = reinterpret_cast<uint4 *>(&x16[i * 16]);
+        d[0] = *reinterpret_cast<uint4 *>(&v[0]);
+        d[1] = *reinterpret_cast<uint4 *>(&v[8]);
+    }
+}
+
+// residual r = x + net - target; loss partials (FP64) and d(loss)/d(net) as
+// BF16 NHWC (16 channels)
+__global__ void k_loss(const float *__restrict__ x, const float *__restrict__ net,
+                       const float *__restrict__ target, bf16 *__restrict__ d16,
+                       double *__restrict__ lpart, int HW, int batch, float scale)
+{
+    const long long n = (long long)batch * HW;
+    double s = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long img = i / HW, p = i - img * HW;
+        __align__(16) bf16 v[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) v[c] = __float2bfloat16_rn(0.f);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const long long k = (img * 3 + c) * HW + p;
+            const float r = x[k] + net[k] - target[k];
+            s += (double)r * r;
+            v[c] = __float2bfloat16_rn(scale * r);
+        }
+        uint4 *d = reinterpret_cast<uint4 *>(&d16[i * 16]);
+        d[0] = *reinterpret_cast<uint4 *>(&v[0]);
+        d[1] = *reinterpret_cast<uint4 *>(&v[8]);
+    }
+    __shared__ double red[256];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) lpart[blockIdx.x] = red[0];
+}
+
+__global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
+                       float *__restrict__ v, int n, float lr, float b1, float b2, float eps,
+                       float c1, float c2)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+// handle fields (FP32 deviation SoA) -> normalised NCHW input, and back
+__global__ void k_gather_state(const float *__restrict__ r, const float *__restrict__ u,
+                               const float *__restrict__ v, float *__restrict__ xo, int HW,
+                               float sr, float su)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < HW; i += gridDim.x * blockDim.x) {
+        xo[i] = r[i] * sr;
+        xo[HW + i] = u[i] * su;
+        xo[2 * HW + i] = v[i] * su;
+    }
+}
+
+__global__ void k_add_correction(float *__restrict__ r, float *__restrict__ u,
+                                 float *__restrict__ v, const float *__restrict__ net, int HW,
+                                 float sr, float su)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < HW; i += gridDim.x * blockDim.x) {
+        r[i] += net[i] / sr;
+        u[i] += net[HW + i] / su;
+        v[i] += net[2 * HW + i] / su;
+    }
+}
+
+}  // namespace
+}  // namespace acm
+
+using namespace acm;
+
+struct acm_closure {
+    int nx = 0, ny = 0, batch = 0;
+    size_t nparam = 0;
+    float scales[3] = {1.f, 1.f, 1.f};
+    float *master = nullptr, *grad = nullptr, *adam_m = nullptr, *adam_v = nullptr;
+    int adam_t = 0;
+    bf16 *A[NL] = {}, *Bm[NL] = {};
+    float *bias[NL] = {};
+    bf16 *x16 = nullptr, *h1 = nullptr, *h2 = nullptr, *d16 = nullptr, *dh2 = nullptr,
+         *dh1 = nullptr;
+    float *net = nullptr, *xbuf = nullptr, *partial = nullptr;
+    double *lpart = nullptr;
+    int loss_blocks = 0, wg_ctas = 0, wg_tiles = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_cl_err;
+
+acm_status cfail(acm_closure *c, acm_status st, const std::string &m)
+{
+    if (c) c->err = m;
+    else g_cl_err = m;
+    return st;
+}
+
+#define CKC(c, call)                                                                        \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return cfail((c), e_ == cudaErrorMemoryAllocation ? ACM_ENOMEM : ACM_ECUDA,      \
+                         std::string(#call) + ": " + cudaGetErrorString(e_));               \
+    } while (0)
+
+size_t n_params()
+{
+    size_t n = 0;
+    for (int l = 0; l < NL; ++l) n += (size_t)COUT[l] * CIN[l] * 9 + COUT[l];
+    return n;
+}
+
+cudaError_t prep(acm_closure *c)
+{
+    k_prep_weights<<<32, 256, 0, c->stream>>>(c->master, c->A[0], c->A[1], c->A[2], c->Bm[1],
+                                              c->Bm[2], c->bias[0], c->bias[1], c->bias[2]);
+    return cudaGetLastError();
+}
+
+// net = closure(x) for normalised x (FP32 NCHW), keeping h1, h2
+cudaError_t forward(acm_closure *c, const float *x)
+{
+    const int HW = c->nx * c->ny;
+    k_pack_nhwc<<<256, 256, 0, c->stream>>>(x, c->x16, HW, c->batch);
+    dim3 grid(c->nx / CTW, c->ny / CTH, c->batch);
+    k_conv<16, 32, OUT_RELU_BF16><<<grid, CTHREADS, 0, c->stream>>>(
+        c->x16, c->A[0], c->bias[0], nullptr, c->h1, c->ny, c->nx, 32);
+    k_conv<32, 32, OUT_RELU_BF16><<<grid, CTHREADS, 0, c->stream>>>(
+        c->h1, c->A[1], c->bias[1], nullptr, c->h2, c->ny, c->nx, 32);
+    k_conv<32, 16, OUT_F32_NCHW><<<grid, CTHREADS, 0, c->stream>>>(
+        c->h2, c->A[2], c->bias[2], nullptr, c->net, c->ny, c->nx, 3);
+    return cudaGetLastError();
+}
+
+// loss and gradients (into c->grad) for input x and target (normalised)
+cudaError_t loss_grad(acm_closure *c, const float *x, const float *target, double *loss)
+{
+    cudaError_t e = forward(c, x);
+    if (e != cudaSuccess) return e;
+    const int HW = c->nx * c->ny;
+    const double nel = 3.0 * HW * c->batch;
+    k_loss<<<c->loss_blocks, 256, 0, c->stream>>>(x, c->net, target, c->d16, c->lpart, HW,
+                                                  c->batch, (float)(2.0 / nel));
+    dim3 grid(c->nx / CTW, c->ny / CTH, c->batch);
+    // data gradients with the ReLU masks of h2 and h1
+    k_conv<16, 32, OUT_MASK_BF16><<<grid, CTHREADS, 0, c->stream>>>(
+        c->d16, c->Bm[2], nullptr, c->h2, c->dh2, c->ny, c->nx, 32);
+    k_conv<32, 32, OUT_MASK_BF16><<<grid, CTHREADS, 0, c->stream>>>(
+        c->dh2, c->Bm[1], nullptr, c->h1, c->dh1, c->ny, c->nx, 32);
+    // weight gradients
+    dim3 wg(c->wg_ctas, c->batch);
+    const int np = c->wg_ctas * c->batch;
+    size_t off = 0;
+    k_wgrad<32, 16><<<wg, CTHREADS, 0, c->stream>>>(c->d16, c->h2, c->partial, c->ny, c->nx,
+                                                   c->wg_tiles);
+    k_wgrad_sum<<<16, 256, 0, c->stream>>>(c->partial, np, CIN[2], COUT[2], CINP[2], COUTP[2],
+                                           c->grad + (COUT[0] * CIN[0] * 9 + COUT[0]) +
+                                               (COUT[1] * CIN[1] * 9 + COUT[1]));
+    k_wgrad<32, 32><<<wg, CTHREADS, 0, c->stream>>>(c->dh2, c->h1, c->partial, c->ny, c->nx,
+                                                   c->wg_tiles);
+    k_wgrad_sum<<<16, 256, 0, c->stream>>>(c->partial, np, CIN[1], COUT[1], CINP[1], COUTP[1],
+                                           c->grad + (COUT[0] * CIN[0] * 9 + COUT[0]));
+    k_wgrad<16, 32><<<wg, CTHREADS, 0, c->stream>>>(c->dh1, c->x16, c->partial, c->ny, c->nx,
+                                                   c->wg_tiles);
+    k_wgrad_sum<<<16, 256, 0, c->stream>>>(c->partial, np, CIN[0], COUT[0], CINP[0], COUTP[0],
+                                           c->grad + off);
+    e = cudaGetLastError();
+    if (e != cudaSuccess || !loss) return e;
+    std::vector<double> lp(c->loss_blocks);
+    e = cudaMemcpyAsync(lp.data(), c->lpart, sizeof(double) * c->loss_blocks,
+                        cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    double s = 0.0;
+    for (double v : lp) s += v;
+    *loss = s / nel;
+    return e;
+}
+
+void release(acm_closure *c)
+{
+    void *ptrs[] = {c->master, c->grad, c->adam_m, c->adam_v, c->x16, c->h1, c->h2, c->d16,
+                    c->dh2, c->dh1, c->net, c->xbuf, c->partial, c->lpart};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    for (int l = 0; l < NL; ++l) {
+        if (c->A[l]) cudaFree(c->A[l]);
+        if (c->Bm[l]) cudaFree(c->Bm[l]);
+        if (c->bias[l]) cudaFree(c->bias[l]);
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t acm_closure_num_params(void) { return n_params(); }
+
+acm_status acm_closure_create(int nx, int ny, int batch, acm_closure **out)
+{
+    if (out) *out = nullptr;
+    if (!out || nx < CTW || ny < CTH || nx % CTW || ny % CTH || batch < 1)
+        return cfail(nullptr, ACM_EINVAL, "closure grid must be a multiple of 16 x 8, batch >= 1");
+    acm_closure *c = new (std::nothrow) acm_closure();
+    if (!c) return cfail(nullptr, ACM_ENOMEM, "host allocation failed");
+    c->nx = nx;
+    c->ny = ny;
+    c->batch = batch;
+    c->nparam = n_params();
+    const size_t HW = (size_t)nx * ny, NB = HW * batch;
+    const int tiles_img = (nx / CTW) * (ny / CTH);
+    c->wg_tiles = 16;
+    c->wg_ctas = (tiles_img + c->wg_tiles - 1) / c->wg_tiles;
+    c->loss_blocks = 512;
+    cudaError_t e = cudaSuccess;
+    auto al = [&](void **p, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+        if (e == cudaSuccess) e = cudaMemset(*p, 0, bytes);
+    };
+    al((void **)&c->master, c->nparam * 4);
+    al((void **)&c->grad, c->nparam * 4);
+    al((void **)&c->adam_m, c->nparam * 4);
+    al((void **)&c->adam_v, c->nparam * 4);
+    for (int l = 0; l < NL; ++l) {
+        al((void **)&c->A[l], (size_t)COUTP[l] * 9 * CINP[l] * 2);
+        if (l > 0) al((void **)&c->Bm[l], (size_t)CINP[l] * 9 * COUTP[l] * 2);
+        al((void **)&c->bias[l], (size_t)COUTP[l] * 4);
+    }
+    al((void **)&c->x16, NB * 16 * 2);
+    al((void **)&c->h1, NB * 32 * 2);
+    al((void **)&c->h2, NB * 32 * 2);
+    al((void **)&c->d16, NB * 16 * 2);
+    al((void **)&c->dh2, NB * 32 * 2);
+    al((void **)&c->dh1, NB * 32 * 2);
+    al((void **)&c->net, NB * 3 * 4);
+    al((void **)&c->xbuf, NB * 3 * 4);
+    al((void **)&c->partial, (size_t)c->wg_ctas * batch * (32 * 9 * 32 + 32) * 4);
+    al((void **)&c->lpart, (size_t)c->loss_blocks * 8);
+    if (e != cudaSuccess) {
+        release(c);
+        delete c;
+        return cfail(nullptr, e == cudaErrorMemoryAllocation ? ACM_ENOMEM : ACM_ECUDA,
+                     std::string("closure allocation: ") + cudaGetErrorString(e));
+    }
+    *out = c;
+    return ACM_OK;
+}
+
+acm_status acm_closure_set_stream(acm_closure *c, void *stream)
+{
+    if (!c) return cfail(nullptr, ACM_EINVAL, "null closure");
+    c->stream = static_cast<cudaStream_t>(stream);
+    return ACM_OK;
+}
+
+acm_status acm_closure_set_scales(acm_closure *c, const float *scales)
+{
+    if (!c || !scales) return cfail(c, ACM_EINVAL, "null argument");
+    for (int i = 0; i < 3; ++i) {
+        if (!(scales[i] > 0.f) || !std::isfinite(scales[i]))
+            return cfail(c, ACM_EINVAL, "scales must be finite and > 0");
+        c->scales[i] = scales[i];
+    }
+    if (c->scales[1] != c->scales[2]) return cfail(c, ACM_EINVAL, "u and v share one scale");
+    return ACM_OK;
+}
+
+acm_status acm_closure_set_weights(acm_closure *c, const float *w, size_t n)
+{
+    if (!c || !w) return cfail(c, ACM_EINVAL, "null argument");
+    if (n != c->nparam) return cfail(c, ACM_EINVAL, "wrong number of parameters");
+    CKC(c, cudaMemcpyAsync(c->master, w, n * 4, cudaMemcpyHostToDevice, c->stream));
+    CKC(c, cudaMemsetAsync(c->adam_m, 0, n * 4, c->stream));
+    CKC(c, cudaMemsetAsync(c->adam_v, 0, n * 4, c->stream));
+    c->adam_t = 0;
+    CKC(c, prep(c));
+    CKC(c, cudaStreamSynchronize(c->stream));
+    return ACM_OK;
+}
+
+acm_status acm_closure_get_weights(acm_closure *c, float *w, size_t n)
+{
+    if (!c || !w) return cfail(c, ACM_EINVAL, "null argument");
+    if (n != c->nparam) return cfail(c, ACM_EINVAL, "wrong number of parameters");
+    CKC(c, cudaMemcpyAsync(w, c->master, n * 4, cudaMemcpyDeviceToHost, c->stream));
+    CKC(c, cudaStreamSynchronize(c->stream));
+    return ACM_OK;
+}
+
+acm_status acm_closure_forward(acm_closure *c, const float *x_dev, float *net_dev)
+{
+    if (!c || !x_dev || !net_dev) return cfail(c, ACM_EINVAL, "null argument");
+    CKC(c, forward(c, x_dev));
+    CKC(c, cudaMemcpyAsync(net_dev, c->net, sizeof(float) * 3 * c->nx * c->ny * c->batch,
+                           cudaMemcpyDeviceToDevice, c->stream));
+    return ACM_OK;
+}
+
+acm_status acm_closure_loss_grad(acm_closure *c, const float *x_dev, const float *target_dev,
+                                 double *loss, float *grad_host)
+{
+    if (!c || !x_dev || !target_dev) return cfail(c, ACM_EINVAL, "null argument");
+    double l = 0.0;
+    CKC(c, loss_grad(c, x_dev, target_dev, &l));
+    if (loss) *loss = l;
+    if (grad_host) {
+        CKC(c, cudaMemcpyAsync(grad_host, c->grad, c->nparam * 4, cudaMemcpyDeviceToHost,
+                               c->stream));
+        CKC(c, cudaStreamSynchronize(c->stream));
+    }
+    return ACM_OK;
+}
+
+acm_status acm_closure_train_step(acm_closure *c, const float *x_dev, const float *target_dev,
+                                  float lr, double *loss)
+{
+    if (!c || !x_dev || !target_dev) return cfail(c, ACM_EINVAL, "null argument");
+    if (!(lr >= 0.f)) return cfail(c, ACM_EINVAL, "lr must be >= 0");
+    CKC(c, loss_grad(c, x_dev, target_dev, loss));
+    c->adam_t += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - std::pow(b1, (float)c->adam_t), c2 = 1.f - std::pow(b2, (float)c->adam_t);
+    k_adam<<<32, 256, 0, c->stream>>>(c->master, c->grad, c->adam_m, c->adam_v, (int)c->nparam,
+                                      lr, b1, b2, 1e-8f, c1, c2);
+    CKC(c, cudaGetLastError());
+    CKC(c, prep(c));
+    return ACM_OK;
+}
+
+acm_status acm_closure_gather(acm_closure *c, acm_handle *h, float *x_dev)
+{
+    if (!c || !h || !x_dev) return cfail(c, ACM_EINVAL, "null argument");
+    if (acm_sync(h) != ACM_OK) return cfail(c, ACM_ESTATE, "solver handle is not healthy");
+    const int HW = c->nx * c->ny;
+    for (int b = 0; b < c->batch; ++b) {
+        float *r, *u, *v;
+        int nx, ny;
+        if (handle_fields_f32(h, b, &r, &u, &v, &nx, &ny) != ACM_OK || nx != c->nx || ny != c->ny)
+            return cfail(c, ACM_EINVAL, "handle run is not an FP32 2D grid of the closure's size");
+        k_gather_state<<<128, 256, 0, c->stream>>>(r, u, v, x_dev + (size_t)b * 3 * HW, HW,
+                                                   c->scales[0], c->scales[1]);
+    }
+    CKC(c, cudaGetLastError());
+    return ACM_OK;
+}
+
+acm_status acm_closure_apply(acm_closure *c, acm_handle *h)
+{
+    if (!c || !h) return cfail(c, ACM_EINVAL, "null argument");
+    acm_status st = acm_closure_gather(c, h, c->xbuf);
+    if (st != ACM_OK) return st;
+    CKC(c, forward(c, c->xbuf));
+    const int HW = c->nx * c->ny;
+    for (int b = 0; b < c->batch; ++b) {
+        float *r, *u, *v;
+        int nx, ny;
+        handle_fields_f32(h, b, &r, &u, &v, &nx, &ny);
+        k_add_correction<<<128, 256, 0, c->stream>>>(r, u, v, c->net + (size_t)b * 3 * HW, HW,
+                                                     c->scales[0], c->scales[1]);
+    }
+    CKC(c, cudaGetLastError());
+    CKC(c, cudaStreamSynchronize(c->stream));  // the handle's next step reads the fields
+    return ACM_OK;
+}
+
+acm_status acm_closure_destroy(acm_closure *c)
+{
+    if (!c) return ACM_OK;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    release(c);
+    delete c;
+    return ACM_OK;
+}
+
+const char *acm_closure_last_error(const acm_closure *c)
+{
+    return c ? c->err.c_str() : g_cl_err.c_str();
+}
+
+}  // extern "C"

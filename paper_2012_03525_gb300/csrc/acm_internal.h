@@ -108,4 +108,9 @@ template <typename T>
 cudaError_t launch_export(const T *src, double *dst, const RunDesc &run, int dim, double shift,
                           cudaStream_t s);
 
+// FP32 2D fields of run `run` in the handle's current buffer (for the
+// learned closure); ACM_EINVAL unless the handle is a 2D FP32 grid.
+acm_status handle_fields_f32(acm_handle *h, int run, float **r, float **u, float **v, int *nx,
+                             int *ny);
+
 }  // namespace acm
