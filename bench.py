@@ -281,6 +281,95 @@ def run_batched_drops(args):
     return 0
 
 
+def run_closure(args):
+    """Learned closure on 2D decaying turbulence (fine 1024^2 FP64 runs of the
+    scheme as reference, coarse 256^2 FP32 runs corrected every 8 steps):
+    trains on the GPU, then compares one-window velocity errors and wall time
+    per window of the corrected coarse run against the plain scheme at 256^2
+    (FP32) and 512^2 (FP64), on held-out initial conditions."""
+    import numpy as np
+    import torch
+    from paper_2012_03525_gb300 import acm, build
+    from paper_2012_03525_gb300 import closure as cl
+    from paper_2012_03525_gb300 import workloads as wl
+    build.build()
+    setup = cl.Setup()
+    B = 4
+    train_seeds = list(wl.TURB_TRAIN_SEEDS)[:args.train_trajectories]
+    test_seeds = list(wl.TURB_TEST_SEEDS)[:B]
+    t0 = time.perf_counter()
+    X, Y = cl.generate(setup, train_seeds, 12, torch, B, reset=True)
+    t_gen = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    clo, losses = cl.train(setup, X, Y, torch, B, epochs=20, lr=1e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    ew = cl.evaluate_windows(setup, clo, test_seeds, 6, torch, B)
+    try:
+        roll = cl.evaluate(setup, clo, test_seeds, windows=6, torch=torch, batch=B)
+    except acm.AcmError as e:  # a corrected free run may blow up
+        roll = {"unstable": str(e)}
+
+    # plain FP64 at 512^2 on the same one-window task, compared at 256^2
+    nc = setup.n_coarse
+    sr, su = setup.scales()
+    fine = cl._fine(setup, test_seeds)
+    mid = acm.Solver([setup.params(2 * nc, acm.FP64) for _ in test_seeds])
+    ref = torch.empty((B, 3, nc, nc), device="cuda", dtype=torch.float32)
+    xm = torch.empty_like(ref)
+    errs = []
+    for _ in range(6):
+        fine.restrict_to(mid, 2)
+        fine.step(setup.window)
+        mid.step(setup.window)
+        fine.restrict_to(None, 4, out_dev=ref.data_ptr(), scales=(sr, su))
+        mid.restrict_to(None, 2, out_dev=xm.data_ptr(), scales=(sr, su))
+        torch.cuda.synchronize()
+        d = (xm[:, 1:] - ref[:, 1:]).double()
+        errs.append(float(torch.sqrt((d * d).sum() / (ref[:, 1:].double() ** 2).sum())))
+
+    def per_window(fn, reps=20):
+        fn()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t) / reps
+
+    coarse = acm.Solver([setup.params(nc, acm.FP32_DEV) for _ in test_seeds])
+    fine.restrict_to(coarse, 4)
+    t_c = per_window(lambda: (coarse.step(setup.window), coarse.sync()))
+    # closure cost: restart from the filtered state each time, so repeated
+    # corrections cannot drift; the restriction's own time is subtracted
+    t_r = per_window(lambda: fine.restrict_to(coarse, 4))
+    t_ra = per_window(lambda: (fine.restrict_to(coarse, 4), clo.apply(coarse)))
+    t_cc = t_c + max(t_ra - t_r, 0.0)
+    t_m = per_window(lambda: (mid.step(setup.window), mid.sync()))
+    t_f = per_window(lambda: (fine.step(setup.window), fine.sync()))
+    res = {
+        "metric": "time-to-eps (one-window velocity error vs filtered 1024^2 FP64 reference)",
+        "value": t_cc, "unit": "s per window (4 runs)", "n_gpus": 1, "higher_is_better": False,
+        "dtype": "bf16 net / f32 solver", "data": "synthetic",
+        "config": {"workload": "learned closure, 2D decaying turbulence, fine 1024^2 FP64, coarse "
+                               "256^2 FP32, window 8 steps, 3-layer 3x3 CNN (32 ch)",
+                   "train_trajectories": len(train_seeds), "windows_per_trajectory": 12,
+                   "test_trajectories": len(test_seeds)},
+        "train": {"loss_first_epoch": losses[0], "loss_last_epoch": losses[-1],
+                  "generate_s": t_gen, "train_s": t_train},
+        "one_window_error": {"coarse256_fp32": ew["plain"], "coarse256_fp32_closure": ew["closure"],
+                             "plain512_fp64": float(np.mean(errs))},
+        "rollout_6_windows_error": roll,
+        "seconds_per_window": {"coarse256_fp32": t_c, "coarse256_fp32_closure": t_cc,
+                               "plain512_fp64": t_m, "plain1024_fp64": t_f},
+    }
+    print(json.dumps(res))
+    for h in (fine, mid, coarse):
+        h.close()
+    clo.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -288,8 +377,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="tgv3d", choices=["tgv3d", "drops"],
-                    help="tgv3d: the bench line; drops: the batched two-phase workload")
+    ap.add_argument("--workload", default="tgv3d", choices=["tgv3d", "drops", "closure"],
+                    help="tgv3d: the bench line; drops: the batched two-phase workload; "
+                         "closure: the learned closure's time-to-eps comparison")
+    ap.add_argument("--train-trajectories", type=int, default=32)
     ap.add_argument("--nruns", type=int, default=512)
     ap.add_argument("--zchunks", type=int, default=env_int("ACM_ZCHUNKS", 0))
     ap.add_argument("--t3y", type=int, default=env_int("ACM_T3Y", 16))
@@ -306,6 +397,8 @@ def main():
         return run_reference(args, rank, world)
     if args.workload == "drops":
         return run_batched_drops(args)
+    if args.workload == "closure":
+        return run_closure(args)
 
     import numpy as np
     import torch

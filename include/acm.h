@@ -178,6 +178,20 @@ acm_status acm_destroy(acm_handle *h);
  * (e.g. after a failed create).  Never NULL. */
 const char *acm_last_error(const acm_handle *h);
 
+/* Box-filter restriction of every run of FINE (2D, single-phase, one grid
+ * size) by FACTOR x FACTOR blocks, with a change of lattice units: the block
+ * means of u, v are multiplied by U_SCALE and of rho - rho0 by RHO_SCALE
+ * (same delta_t, delta_x times FACTOR: U_SCALE = 1/FACTOR, and the pressure
+ * p = c_s^2 (rho - rho0) is kept when RHO_SCALE = 1/FACTOR^2).  The result
+ * goes into the current fields of COARSE (same number of runs, grid =
+ * fine / factor; resets its step counter like acm_set_fields) and/or into
+ * OUT_DEV as normalised FP32 [nruns][3][ny/factor][nx/factor]
+ * (s_rho (rho - rho0), s_u u, s_u v with scales3 = {s_rho, s_u, s_u}).  Used
+ * to start coarse runs from, and to build training targets of the learned
+ * closure from, fine runs.  Synchronous. */
+acm_status acm_restrict(acm_handle *fine, acm_handle *coarse, int factor, double u_scale,
+                        double rho_scale, float *out_dev, const float *scales3);
+
 /* ---- learned closure ------------------------------------------------------
  * A small convolutional network that corrects a coarse-grid state after
  * solver steps: three periodic 3x3 convolutions, channels 3 -> 32 -> 32 -> 3,
@@ -199,12 +213,17 @@ acm_status acm_closure_create(int nx, int ny, int batch, acm_closure **out);
 acm_status acm_closure_set_stream(acm_closure *c, void *stream);
 /* normalisation scales s_rho, s_u, s_u (s_u shared by u and v) */
 acm_status acm_closure_set_scales(acm_closure *c, const float *scales3);
+/* per-channel weights of the loss, default {1, 1, 1}; a channel of weight 0
+ * is neither fitted nor corrected by acm_closure_apply (use {0, 1, 1} to
+ * leave the density deviation, whose acoustic content differs between grids
+ * of different lattice speed, to the scheme) */
+acm_status acm_closure_set_loss_weights(acm_closure *c, const float *w3);
 /* host FP32 weights in, resets the Adam state; or weights out */
 acm_status acm_closure_set_weights(acm_closure *c, const float *w, size_t n);
 acm_status acm_closure_get_weights(acm_closure *c, float *w, size_t n);
 /* net(x) for normalised x -> net_dev (same layout), asynchronous */
 acm_status acm_closure_forward(acm_closure *c, const float *x_dev, float *net_dev);
-/* loss = mean((x + net(x) - target)^2) and its gradient (grad_host may be
+/* loss = mean((w_c (x + net(x) - target))^2) and its gradient (grad_host may be
  * NULL; n = acm_closure_num_params()); synchronous */
 acm_status acm_closure_loss_grad(acm_closure *c, const float *x_dev, const float *target_dev,
                                  double *loss, float *grad_host);

@@ -21,8 +21,8 @@ TUNE_ZCHUNKS, TUNE_T3Y, TUNE_GRAPH_STEPS, TUNE_BLOCKS = 1, 2, 3, 4
 EXPORTS = ["acm_create", "acm_batch_create", "acm_set_stream", "acm_nruns", "acm_set_fields",
            "acm_step", "acm_sync", "acm_fields", "acm_reduce_mass", "acm_set_tuning",
            "acm_step_count", "acm_destroy", "acm_last_error", "acm_get_tuning", "acm_autotune",
-           "acm_closure_num_params", "acm_closure_create", "acm_closure_set_stream",
-           "acm_closure_set_scales", "acm_closure_set_weights", "acm_closure_get_weights",
+           "acm_restrict", "acm_closure_num_params", "acm_closure_create", "acm_closure_set_stream",
+           "acm_closure_set_scales", "acm_closure_set_loss_weights", "acm_closure_set_weights", "acm_closure_get_weights",
            "acm_closure_forward", "acm_closure_loss_grad", "acm_closure_train_step",
            "acm_closure_gather", "acm_closure_apply", "acm_closure_destroy",
            "acm_closure_last_error", "acm_reduce_mass_noalloc",
@@ -82,11 +82,14 @@ def load():
                                     [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p],
                                     ctypes.c_int),
         "acm_noalloc_last_error": ([], ctypes.c_char_p),
+        "acm_restrict": ([H, H, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_void_p,
+                          ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
         "acm_closure_num_params": ([], ctypes.c_size_t),
         "acm_closure_create": ([ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                 ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
         "acm_closure_set_stream": ([H, ctypes.c_void_p], ctypes.c_int),
         "acm_closure_set_scales": ([H, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
+        "acm_closure_set_loss_weights": ([H, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
         "acm_closure_set_weights": ([H, ctypes.POINTER(ctypes.c_float), ctypes.c_size_t],
                                     ctypes.c_int),
         "acm_closure_get_weights": ([H, ctypes.POINTER(ctypes.c_float), ctypes.c_size_t],
@@ -238,6 +241,18 @@ class Solver:
         self._check(self._lib.acm_reduce_mass(self._h, _dptr(out)))
         return out.reshape(self.nruns, 8) if self.nruns > 1 else out
 
+    def restrict_to(self, coarse=None, factor=4, out_dev=None, scales=(1.0, 1.0), u_scale=None,
+                    rho_scale=None):
+        """Box-filter this (fine) handle's runs into ``coarse`` and/or a
+        normalised device buffer (acm_restrict); by default the lattice units
+        change with delta_x (u / factor, rho' / factor^2)."""
+        us = 1.0 / factor if u_scale is None else u_scale
+        rs = 1.0 / factor ** 2 if rho_scale is None else rho_scale
+        sc = (ctypes.c_float * 3)(scales[0], scales[1], scales[1])
+        self._check(self._lib.acm_restrict(self._h, coarse._h if coarse is not None else None,
+                                           factor, us, rs,
+                                           ctypes.c_void_p(out_dev) if out_dev else None, sc))
+
     def step_count(self):
         return self._lib.acm_step_count(self._h)
 
@@ -283,6 +298,10 @@ class Closure:
     def set_scales(self, s_rho, s_u):
         arr = (ctypes.c_float * 3)(s_rho, s_u, s_u)
         self._check(self._lib.acm_closure_set_scales(self._c, arr))
+
+    def set_loss_weights(self, w_rho, w_u):
+        arr = (ctypes.c_float * 3)(w_rho, w_u, w_u)
+        self._check(self._lib.acm_closure_set_loss_weights(self._c, arr))
 
     def set_weights(self, w):
         w = np.ascontiguousarray(w, dtype=np.float32)

@@ -408,6 +408,67 @@ acm_status check_flags(acm_handle *h)
 
 }  // namespace
 
+namespace {
+
+// box-filter restriction of fine fields onto a coarse grid (2D, one run per
+// blockIdx.y): coarse = mean of the factor x factor fine nodes it covers
+template <typename TF, typename TC>
+__global__ void k_restrict(const RunDesc *__restrict__ fr, Fields<TF> fine, const RunDesc *cr,
+                           Fields<TC> coarse, int factor, double us, double rs, float *out,
+                           float sr, float su, int nxc, int nyc)
+{
+    const int run = blockIdx.y;
+    const RunDesc &F = fr[run];
+    const long long nc = (long long)nxc * nyc;
+    const double inv = 1.0 / ((double)factor * factor);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nc;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int yc = (int)(i / nxc), xc = (int)(i - (long long)yc * nxc);
+        double sr_ = 0.0, su_ = 0.0, sv_ = 0.0;
+        for (int a = 0; a < factor; ++a)
+            for (int b = 0; b < factor; ++b) {
+                const long long k = F.off + (long long)(yc * factor + a) * F.nx + xc * factor + b;
+                sr_ += (double)fine.f[F_R][k];
+                su_ += (double)fine.f[F_U][k];
+                sv_ += (double)fine.f[F_V][k];
+            }
+        // unit change to the coarse lattice: velocity times us, density
+        // deviation (the pressure signal) times rs
+        const double r = sr_ * inv * rs, u = su_ * inv * us, v = sv_ * inv * us;
+        if (cr) {
+            const RunDesc &C = cr[run];
+            const long long k = C.off + i;
+            coarse.f[F_R][k] = (TC)r;
+            coarse.f[F_U][k] = (TC)u;
+            coarse.f[F_V][k] = (TC)v;
+        }
+        if (out) {
+            float *o = out + (long long)run * 3 * nc;
+            o[i] = (float)(r * sr);
+            o[nc + i] = (float)(u * su);
+            o[2 * nc + i] = (float)(v * su);
+        }
+    }
+}
+
+template <typename TF, typename TC>
+cudaError_t restrict_launch(acm_handle *f, acm_handle *c, int factor, double us, double rs,
+                            float *out, float sr, float su, int nxc, int nyc)
+{
+    Fields<TF> ff;
+    Fields<TC> cf;
+    for (int k = 0; k < NFIELD; ++k) {
+        ff.f[k] = static_cast<TF *>(f->buf[f->cur][k]);
+        cf.f[k] = c ? static_cast<TC *>(c->buf[c->cur][k]) : nullptr;
+    }
+    dim3 grid(256, f->nruns);
+    k_restrict<TF, TC><<<grid, 256, 0, f->stream>>>(f->druns, ff, c ? c->druns : nullptr, cf,
+                                                    factor, us, rs, out, sr, su, nxc, nyc);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
 namespace acm {
 acm_status handle_fields_f32(acm_handle *h, int run, float **r, float **u, float **v, int *nx,
                              int *ny)
@@ -728,6 +789,50 @@ acm_status acm_reduce_mass(acm_handle *h, double *out)
     CK(h, cudaMemcpyAsync(out, h->dout, sizeof(double) * 8 * h->nruns, cudaMemcpyDeviceToHost,
                           h->stream));
     return check_flags(h);
+}
+
+acm_status acm_restrict(acm_handle *fine, acm_handle *coarse, int factor, double u_scale,
+                        double rho_scale, float *out_dev, const float *scales3)
+{
+    if (!fine || factor < 1 || (!coarse && !out_dev) || (out_dev && !scales3))
+        return fail(fine, ACM_EINVAL, "bad restrict arguments");
+    if (fine->dim != 2) return fail(fine, ACM_EINVAL, "restriction is 2D only");
+    const RunDesc &F0 = fine->runs[0];
+    if (F0.nx % factor || F0.ny % factor) return fail(fine, ACM_EINVAL, "factor must divide the grid");
+    const int nxc = F0.nx / factor, nyc = F0.ny / factor;
+    for (int r = 0; r < fine->nruns; ++r)
+        if (fine->runs[r].nx != F0.nx || fine->runs[r].ny != F0.ny)
+            return fail(fine, ACM_EINVAL, "fine runs must share one grid size");
+    if (coarse) {
+        if (coarse->dim != 2 || coarse->nruns != fine->nruns || coarse->two_phase)
+            return fail(coarse, ACM_EINVAL, "coarse handle must be 2D single-phase, same runs");
+        for (int r = 0; r < coarse->nruns; ++r)
+            if (coarse->runs[r].nx != nxc || coarse->runs[r].ny != nyc)
+                return fail(coarse, ACM_EINVAL, "coarse grid must be the fine grid / factor");
+    }
+    CK(fine, cudaSetDevice(fine->device));
+    if (coarse) CK(fine, cudaStreamSynchronize(coarse->stream));
+    const float sr = out_dev ? scales3[0] : 1.f, su = out_dev ? scales3[1] : 1.f;
+    cudaError_t e;
+    const bool f64 = fine->prec == ACM_FP64, c64 = coarse ? coarse->prec == ACM_FP64 : false;
+    const double us = u_scale, rs = rho_scale;
+    if (f64 && c64)
+        e = restrict_launch<double, double>(fine, coarse, factor, us, rs, out_dev, sr, su, nxc, nyc);
+    else if (f64)
+        e = restrict_launch<double, float>(fine, coarse, factor, us, rs, out_dev, sr, su, nxc, nyc);
+    else if (c64)
+        e = restrict_launch<float, double>(fine, coarse, factor, us, rs, out_dev, sr, su, nxc, nyc);
+    else
+        e = restrict_launch<float, float>(fine, coarse, factor, us, rs, out_dev, sr, su, nxc, nyc);
+    if (e != cudaSuccess) return cuda_fail(fine, e, "restriction kernel");
+    CK(fine, cudaStreamSynchronize(fine->stream));
+    if (coarse) {
+        coarse->steps = 0;
+        coarse->sticky = 0;
+        for (int r = 0; r < coarse->nruns; ++r) coarse->have_fields[r] = 1;
+        CK(coarse, cudaMemset(coarse->derr, 0, sizeof(unsigned)));
+    }
+    return ACM_OK;
 }
 
 acm_status acm_destroy(acm_handle *h)

@@ -332,8 +332,10 @@ __global__ void k_pack_nhwc(const float *__restrict__ xin, bf16 *__restrict__ x1
 // BF16 NHWC (16 channels)
 __global__ void k_loss(const float *__restrict__ x, const float *__restrict__ net,
                        const float *__restrict__ target, bf16 *__restrict__ d16,
-                       double *__restrict__ lpart, int HW, int batch, float scale)
+                       double *__restrict__ lpart, int HW, int batch, float scale, float w0,
+                       float w1, float w2)
 {
+    const float wc[3] = {w0, w1, w2};
     const long long n = (long long)batch * HW;
     double s = 0.0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -345,9 +347,9 @@ __global__ void k_loss(const float *__restrict__ x, const float *__restrict__ ne
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const long long k = (img * 3 + c) * HW + p;
-            const float r = x[k] + net[k] - target[k];
+            const float r = wc[c] * (x[k] + net[k] - target[k]);
             s += (double)r * r;
-            v[c] = __float2bfloat16_rn(scale * r);
+            v[c] = __float2bfloat16_rn(scale * wc[c] * r);
         }
         uint4 *d = reinterpret_cast<uint4 *>(&d16[i * 16]);
         d[0] = *reinterpret_cast<uint4 *>(&v[0]);
@@ -391,10 +393,10 @@ __global__ void k_gather_state(const float *__restrict__ r, const float *__restr
 
 __global__ void k_add_correction(float *__restrict__ r, float *__restrict__ u,
                                  float *__restrict__ v, const float *__restrict__ net, int HW,
-                                 float sr, float su)
+                                 float sr, float su, float w0)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < HW; i += gridDim.x * blockDim.x) {
-        r[i] += net[i] / sr;
+        if (w0 != 0.f) r[i] += net[i] / sr;
         u[i] += net[HW + i] / su;
         v[i] += net[2 * HW + i] / su;
     }
@@ -409,6 +411,7 @@ struct acm_closure {
     int nx = 0, ny = 0, batch = 0;
     size_t nparam = 0;
     float scales[3] = {1.f, 1.f, 1.f};
+    float weights[3] = {1.f, 1.f, 1.f};  // loss weight per channel (0 = not corrected)
     float *master = nullptr, *grad = nullptr, *adam_m = nullptr, *adam_v = nullptr;
     int adam_t = 0;
     bf16 *A[NL] = {}, *Bm[NL] = {};
@@ -478,7 +481,8 @@ cudaError_t loss_grad(acm_closure *c, const float *x, const float *target, doubl
     const int HW = c->nx * c->ny;
     const double nel = 3.0 * HW * c->batch;
     k_loss<<<c->loss_blocks, 256, 0, c->stream>>>(x, c->net, target, c->d16, c->lpart, HW,
-                                                  c->batch, (float)(2.0 / nel));
+                                                  c->batch, (float)(2.0 / nel), c->weights[0],
+                                                  c->weights[1], c->weights[2]);
     dim3 grid(c->nx / CTW, c->ny / CTH, c->batch);
     // data gradients with the ReLU masks of h2 and h1
     k_conv<16, 32, OUT_MASK_BF16><<<grid, CTHREADS, 0, c->stream>>>(
@@ -602,6 +606,17 @@ acm_status acm_closure_set_scales(acm_closure *c, const float *scales)
     return ACM_OK;
 }
 
+acm_status acm_closure_set_loss_weights(acm_closure *c, const float *w3)
+{
+    if (!c || !w3) return cfail(c, ACM_EINVAL, "null argument");
+    for (int i = 0; i < 3; ++i) {
+        if (!(w3[i] >= 0.f) || !std::isfinite(w3[i]))
+            return cfail(c, ACM_EINVAL, "loss weights must be finite and >= 0");
+        c->weights[i] = w3[i];
+    }
+    return ACM_OK;
+}
+
 acm_status acm_closure_set_weights(acm_closure *c, const float *w, size_t n)
 {
     if (!c || !w) return cfail(c, ACM_EINVAL, "null argument");
@@ -693,7 +708,7 @@ acm_status acm_closure_apply(acm_closure *c, acm_handle *h)
         int nx, ny;
         handle_fields_f32(h, b, &r, &u, &v, &nx, &ny);
         k_add_correction<<<128, 256, 0, c->stream>>>(r, u, v, c->net + (size_t)b * 3 * HW, HW,
-                                                     c->scales[0], c->scales[1]);
+                                                     c->scales[0], c->scales[1], c->weights[0]);
     }
     CKC(c, cudaGetLastError());
     CKC(c, cudaStreamSynchronize(c->stream));  // the handle's next step reads the fields
