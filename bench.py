@@ -402,7 +402,7 @@ def main():
 
     import numpy as np
     import torch
-    from paper_2012_03525_gb300 import acm, build
+    from paper_2012_03525_gb300 import acm, build, multirank
     from paper_2012_03525_gb300 import workloads as wl
 
     torch.cuda.set_device(local)
@@ -442,10 +442,7 @@ def main():
         barrier()
     ms = ev0.elapsed_time(ev1)
     solver.sync()  # raises on blow-up
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = multirank.max_over_ranks(ms, dist, device="cuda")
     diag = solver.reduce()
 
     # end to end through the C ABI with pinned host buffers: upload the initial
@@ -459,18 +456,14 @@ def main():
     diag_e2e = solver.reduce()
     solver.fields_raw(0, [o.data_ptr() for o in outs] + [None])
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = multirank.max_over_ranks(time.perf_counter() - t0, dist, device="cuda")
 
     if rank != 0:
         solver.close()
         dist.destroy_process_group()
         return 0
 
-    glups = nodes * args.steps * world / (ms / 1e3) / 1e9
+    glups = multirank.job_throughput(nodes, args.steps, world, ms / 1e3)
     per_launch_s = ms / 1e3 / args.steps
     peak, peak_kind = measured_peaks()
     achieved = BYTES_PER_LU_FP32 * nodes / per_launch_s / 1e9
@@ -491,7 +484,7 @@ def main():
                      "frac": achieved / peak, "peak_kind": f"{peak_kind} copy bandwidth",
                      "traffic": profiled_traffic(),
                      "algorithmic_bytes_per_launch": BYTES_PER_LU_FP32 * nodes},
-        "e2e": {"value": nodes * args.steps * world / e2e_s / 1e9, "unit": "GLUPS",
+        "e2e": {"value": multirank.job_throughput(nodes, args.steps, world, e2e_s), "unit": "GLUPS",
                 "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                 "seconds": e2e_s},
         "gpu_launches": args.steps,
