@@ -20,6 +20,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I", os.path.join(os.path.dirname(HERE), "include")]
+# extra nvcc flags (e.g. -D switches for launch-bound experiments)
+FLAGS += os.environ.get("ACM_NVCC_EXTRA", "").split()
 
 
 def _deps():

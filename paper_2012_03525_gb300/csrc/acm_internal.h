@@ -102,6 +102,10 @@ cudaError_t launch_reduce(const RunDesc *druns, int nruns, int dim, Fields<T> cu
                           double *dout, cudaStream_t s);
 
 template <typename T>
+cudaError_t launch_scan_nonfinite(const T *a, const T *b, long long n, unsigned *err,
+                                  cudaStream_t s);
+
+template <typename T>
 cudaError_t launch_import(const double *src, T *dst, const RunDesc &run, int dim, double shift,
                           cudaStream_t s);
 template <typename T>

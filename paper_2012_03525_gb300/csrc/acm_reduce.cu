@@ -132,7 +132,32 @@ __global__ void k_export(const T *__restrict__ src, double *__restrict__ dst, Ru
         dst[i] = (double)src[storage_index(R, dim, i)] + shift;
 }
 
+// blow-up detection for kernels that do not flag it themselves: any
+// non-finite value in two fields sets ERR_NONFINITE
+template <typename T>
+__global__ void k_scan_nonfinite(const T *__restrict__ a, const T *__restrict__ b, long long n,
+                                 unsigned *err)
+{
+    bool bad = false;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        bad |= !isfinite(a[i]) || !isfinite(b[i]);
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(err, ERR_NONFINITE);
+}
+
 }  // namespace
+
+template <typename T>
+cudaError_t launch_scan_nonfinite(const T *a, const T *b, long long n, unsigned *err,
+                                  cudaStream_t s)
+{
+    k_scan_nonfinite<T><<<1216, 256, 0, s>>>(a, b, n, err);
+    return cudaGetLastError();
+}
+template cudaError_t launch_scan_nonfinite<float>(const float *, const float *, long long,
+                                                  unsigned *, cudaStream_t);
+template cudaError_t launch_scan_nonfinite<double>(const double *, const double *, long long,
+                                                   unsigned *, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_reduce(const RunDesc *druns, int nruns, int dim, Fields<T> cur, const T *pu,

@@ -20,6 +20,8 @@
 //     d_a rho^{n+1} - d_a rho^n of Eq. (2.11) is a centred difference of
 //     Delta rho.
 //   * Eq. (2.11) for plane z; u^{n+1} = u + (RHS - Delta rho u) / rho^{n+1}.
+//   * The kernel does not test its outputs for blow-up; the library scans
+//     the fields for non-finite values when the caller synchronises.
 // Storage is padded by T3PAD ghost nodes in x and y (not in z).  Every output
 // node on the first/last two columns/rows is also written to its periodic
 // image in the ghost layers, so the next step's TMA boxes never wrap in x/y;
@@ -82,7 +84,10 @@ struct Prec;
 template <>
 struct Prec<float> {
     static constexpr int NSLOT = 5;
-    static constexpr int MINB = 3;  // CTAs per SM (of 256 threads) to aim for
+#ifndef ACM_STEP3D_MINB
+#define ACM_STEP3D_MINB 2
+#endif
+    static constexpr int MINB = ACM_STEP3D_MINB;  // CTAs per SM (of 256 threads) to aim for
     static __device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
 };
 template <>
@@ -115,7 +120,8 @@ struct Col {
 
 // Eq. (2.11) for one node from its 7-point neighbourhood (index order
 // C, E, W, N, S, U, D) of rho', u, v, w and Delta rho; returns the new state.
-template <typename T>
+// Written as chains of fused multiply-adds.
+template <typename T, bool GRAV>
 __device__ __forceinline__ void node_update(const T (&r)[7], const T (&u)[7], const T (&v)[7],
                                             const T (&w)[7], const T (&d)[7], T rho0, T hdt,
                                             T hdtcs2, T nudt, T hsatm, T dt, T gx, T gy, T gz,
@@ -129,25 +135,39 @@ __device__ __forceinline__ void node_update(const T (&r)[7], const T (&u)[7], co
         my[k] = q * v[k];
         mz[k] = q * w[k];
     }
-    // centred flux differences d_b(rho u_a u_b) (times 2) and Laplacians
-    const T fx = (mx[1] * u[1] - mx[2] * u[2]) + (mx[3] * v[3] - mx[4] * v[4]) +
-                 (mx[5] * w[5] - mx[6] * w[6]);
-    const T fy = (my[1] * u[1] - my[2] * u[2]) + (my[3] * v[3] - my[4] * v[4]) +
-                 (my[5] * w[5] - my[6] * w[6]);
-    const T fz = (mz[1] * u[1] - mz[2] * u[2]) + (mz[3] * v[3] - mz[4] * v[4]) +
-                 (mz[5] * w[5] - mz[6] * w[6]);
-    const T lx = (mx[1] + mx[2]) + (mx[3] + mx[4]) + (mx[5] + mx[6]) - T(6) * mx[0];
-    const T ly = (my[1] + my[2]) + (my[3] + my[4]) + (my[5] + my[6]) - T(6) * my[0];
-    const T lz = (mz[1] + mz[2]) + (mz[3] + mz[4]) + (mz[5] + mz[6]) - T(6) * mz[0];
+    // twice the centred differences d_b(rho u_a u_b)
+    auto flux = [&](const T (&m)[7]) {
+        T f = m[1] * u[1];
+        f = fma(-m[2], u[2], f);
+        f = fma(m[3], v[3], f);
+        f = fma(-m[4], v[4], f);
+        f = fma(m[5], w[5], f);
+        return fma(-m[6], w[6], f);
+    };
+    auto lap = [&](const T (&m)[7]) {
+        return fma(T(-6), m[0], ((m[1] + m[2]) + (m[3] + m[4])) + (m[5] + m[6]));
+    };
     const T rho1 = rho0 + r[0] + d[0];
     const T inv = Prec<T>::recip(rho1);
-    const T fb = dt * rho1;
-    const T rx = -hdt * fx - hdtcs2 * (r[1] - r[2]) + nudt * lx - hsatm * (d[1] - d[2]) + fb * gx;
-    const T ry = -hdt * fy - hdtcs2 * (r[3] - r[4]) + nudt * ly - hsatm * (d[3] - d[4]) + fb * gy;
-    const T rz = -hdt * fz - hdtcs2 * (r[5] - r[6]) + nudt * lz - hsatm * (d[5] - d[6]) + fb * gz;
-    un = u[0] + (rx - d[0] * u[0]) * inv;
-    vn = v[0] + (ry - d[0] * v[0]) * inv;
-    wn = w[0] + (rz - d[0] * w[0]) * inv;
+    T rx = nudt * lap(mx), ry = nudt * lap(my), rz = nudt * lap(mz);
+    rx = fma(-hdt, flux(mx), rx);
+    ry = fma(-hdt, flux(my), ry);
+    rz = fma(-hdt, flux(mz), rz);
+    rx = fma(-hdtcs2, r[1] - r[2], rx);
+    ry = fma(-hdtcs2, r[3] - r[4], ry);
+    rz = fma(-hdtcs2, r[5] - r[6], rz);
+    rx = fma(-hsatm, d[1] - d[2], rx);
+    ry = fma(-hsatm, d[3] - d[4], ry);
+    rz = fma(-hsatm, d[5] - d[6], rz);
+    if (GRAV) {
+        const T fb = dt * rho1;
+        rx = fma(fb, gx, rx);
+        ry = fma(fb, gy, ry);
+        rz = fma(fb, gz, rz);
+    }
+    un = fma(fma(-d[0], u[0], rx), inv, u[0]);
+    vn = fma(fma(-d[0], v[0], ry), inv, v[0]);
+    wn = fma(fma(-d[0], w[0], rz), inv, w[0]);
     rn = r[0] + d[0];
 }
 
@@ -179,7 +199,7 @@ __device__ __forceinline__ void store_images(Fields<T> out, long long gi, int gx
         }
 }
 
-template <typename T, int TY>
+template <typename T, int TY, bool GRAV>
 __global__ void __launch_bounds__(T3X *TY / 2, Prec<T>::MINB * 16 / TY)
     k_step3d(const __grid_constant__ CUtensorMap mr, const __grid_constant__ CUtensorMap mu_,
              const __grid_constant__ CUtensorMap mv, const __grid_constant__ CUtensorMap mw,
@@ -303,7 +323,6 @@ __global__ void __launch_bounds__(T3X *TY / 2, Prec<T>::MINB * 16 / TY)
         }
     };
 
-    bool nonfinite = false;
     Col<T> Q[NSLOT];   // own-node values of the plane held in slot s
     T D[NSLOT][2];     // own-node Delta rho of the plane held in slot s
 
@@ -331,17 +350,39 @@ __global__ void __launch_bounds__(T3X *TY / 2, Prec<T>::MINB * 16 / TY)
         if (tid == 0 && zbeg + NSLOT - 2 <= zlast) issue(0, zbeg + NSLOT - 2, x0, y0);
 
         const int gx = x0 + tx, gya = y0 + ya, gyb = gya + 1;
+        // CTA-uniform: every node of the tile is inside the grid and none of
+        // them has a periodic image in the ghost layers
+        const bool plain_tile = x0 >= T3PAD && x0 + T3X <= nx - T3PAD && y0 >= T3PAD &&
+                                y0 + TY <= ny - T3PAD;
         const bool own_a = gx < nx && gya < ny, own_b = gx < nx && gyb < ny;
         const bool edge = gx < T3PAD || gx >= nx - T3PAD || gya < T3PAD || gyb >= ny - T3PAD;
         const long long base_a = R.off + (long long)(gya + T3PAD) * PX + (gx + T3PAD);
-        auto store = [&](long long gi, int gy, T rn, T un, T vn, T wn) {
-            out.f[F_R][gi] = rn;
-            out.f[F_U][gi] = un;
-            out.f[F_V][gi] = vn;
-            out.f[F_W][gi] = wn;
-            if (edge) store_images<T>(out, gi, gx, gy, nx, ny, PX, rn, un, vn, wn);
-            // a non-finite value in any field makes the sum non-finite
-            nonfinite |= !isfinite(rn + un + vn + wn);
+        auto store2 = [&](long long ga, T ra, T ua, T va, T wa, T rb, T ub, T vb, T wb) {
+            if (plain_tile) {
+                out.f[F_R][ga] = ra;
+                out.f[F_U][ga] = ua;
+                out.f[F_V][ga] = va;
+                out.f[F_W][ga] = wa;
+                out.f[F_R][ga + PX] = rb;
+                out.f[F_U][ga + PX] = ub;
+                out.f[F_V][ga + PX] = vb;
+                out.f[F_W][ga + PX] = wb;
+                return;
+            }
+            if (own_a) {
+                out.f[F_R][ga] = ra;
+                out.f[F_U][ga] = ua;
+                out.f[F_V][ga] = va;
+                out.f[F_W][ga] = wa;
+                if (edge) store_images<T>(out, ga, gx, gya, nx, ny, PX, ra, ua, va, wa);
+            }
+            if (own_b) {
+                out.f[F_R][ga + PX] = rb;
+                out.f[F_U][ga + PX] = ub;
+                out.f[F_V][ga + PX] = vb;
+                out.f[F_W][ga + PX] = wb;
+                if (edge) store_images<T>(out, ga + PX, gx, gyb, nx, ny, PX, rb, ub, vb, wb);
+            }
         };
 
         // one z step for plane z = zg + J, with (zg - zbeg) a multiple of NSLOT
@@ -362,16 +403,15 @@ __global__ void __launch_bounds__(T3X *TY / 2, Prec<T>::MINB * 16 / TY)
             const T *pr = S + S0 * 4 * PE, *pu = pr + PE, *pv = pr + 2 * PE, *pw = pr + 3 * PE;
             const T *dz = SD + (z & 1) * P1;
             const Col<T> &Xm = Q[SM], &X0 = Q[S0], &Xp = Q[S1];
-            T rn, un, vn, wn;
+            T ra, ua, va, wa, rb, ub, vb, wb;
             {   // lower node a: N neighbour is node b
                 const T r[7] = {X0.r[0], pr[ca + 1], pr[ca - 1], X0.r[1], pr[ca - RW], Xp.r[0], Xm.r[0]};
                 const T u[7] = {X0.u[0], pu[ca + 1], pu[ca - 1], X0.u[1], pu[ca - RW], Xp.u[0], Xm.u[0]};
                 const T v[7] = {X0.v[0], pv[ca + 1], pv[ca - 1], X0.v[1], pv[ca - RW], Xp.v[0], Xm.v[0]};
                 const T w[7] = {X0.w[0], pw[ca + 1], pw[ca - 1], X0.w[1], pw[ca - RW], Xp.w[0], Xm.w[0]};
                 const T d[7] = {D[S0][0], dz[da + 1], dz[da - 1], D[S0][1], dz[da - RW1], D[S1][0], D[SM][0]};
-                node_update<T>(r, u, v, w, d, rho0, hdt, hdtcs2, nudt, hsatm, dt, gfx, gfy, gfz,
-                               rn, un, vn, wn);
-                if (own_a) store(base_a + (long long)z * PXY, gya, rn, un, vn, wn);
+                node_update<T, GRAV>(r, u, v, w, d, rho0, hdt, hdtcs2, nudt, hsatm, dt, gfx, gfy,
+                                     gfz, ra, ua, va, wa);
             }
             {   // upper node b: S neighbour is node a
                 const T r[7] = {X0.r[1], pr[cb + 1], pr[cb - 1], pr[cb + RW], X0.r[0], Xp.r[1], Xm.r[1]};
@@ -379,10 +419,10 @@ __global__ void __launch_bounds__(T3X *TY / 2, Prec<T>::MINB * 16 / TY)
                 const T v[7] = {X0.v[1], pv[cb + 1], pv[cb - 1], pv[cb + RW], X0.v[0], Xp.v[1], Xm.v[1]};
                 const T w[7] = {X0.w[1], pw[cb + 1], pw[cb - 1], pw[cb + RW], X0.w[0], Xp.w[1], Xm.w[1]};
                 const T d[7] = {D[S0][1], dz[db + 1], dz[db - 1], dz[db + RW1], D[S0][0], D[S1][1], D[SM][1]};
-                node_update<T>(r, u, v, w, d, rho0, hdt, hdtcs2, nudt, hsatm, dt, gfx, gfy, gfz,
-                               rn, un, vn, wn);
-                if (own_b) store(base_a + PX + (long long)z * PXY, gyb, rn, un, vn, wn);
+                node_update<T, GRAV>(r, u, v, w, d, rho0, hdt, hdtcs2, nudt, hsatm, dt, gfx, gfy,
+                                     gfz, rb, ub, vb, wb);
             }
+            store2(base_a + (long long)z * PXY, ra, ua, va, wa, rb, ub, vb, wb);
         };
 
         for (int zg = zbeg; zg < zend; zg += NSLOT) {
@@ -401,20 +441,19 @@ __global__ void __launch_bounds__(T3X *TY / 2, Prec<T>::MINB * 16 / TY)
         __syncthreads();  // every read of this chunk's planes is done
         if (*s_abort) break;
     }
-    if (nonfinite) atomicOr(err, ERR_NONFINITE);
 }
 
-template <typename T, int TY>
-int max_blocks()
+template <typename T, int TY, bool GRAV>
+int max_blocks_g()
 {
     static int cached = -1;
     if (cached < 0) {
         using G = Geo<T, TY>;
-        cudaFuncSetAttribute(k_step3d<T, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_step3d<T, TY, GRAV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              G::SMEM);
         int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step3d<T, TY>, G::NT, G::SMEM) !=
-            cudaSuccess)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step3d<T, TY, GRAV>, G::NT,
+                                                          G::SMEM) != cudaSuccess)
             nb = 1;
         cached = nb > 0 ? nb : 1;
     }
@@ -422,11 +461,19 @@ int max_blocks()
 }
 
 template <typename T, int TY>
+int max_blocks()
+{
+    max_blocks_g<T, TY, true>();
+    return max_blocks_g<T, TY, false>();
+}
+
+template <typename T, int TY>
 cudaError_t launch(const CUtensorMap *m, Fields<T> out, const RunDesc &run, unsigned *derr,
                    int zchunks, int sms, cudaStream_t s)
 {
     using G = Geo<T, TY>;
-    const int per_sm = max_blocks<T, TY>();
+    const bool grav = run.g[0] != 0.0 || run.g[1] != 0.0 || run.g[2] != 0.0;
+    const int per_sm = grav ? max_blocks_g<T, TY, true>() : max_blocks_g<T, TY, false>();
     // chunks of zc planes; by default 16 (short enough for many CTAs, long
     // enough that the 4 extra planes per chunk cost little)
     const int nzc = zchunks > 0 ? std::min(zchunks, run.nz) : std::max(1, (run.nz + 15) / 16);
@@ -437,8 +484,12 @@ cudaError_t launch(const CUtensorMap *m, Fields<T> out, const RunDesc &run, unsi
     // resident together work on neighbouring columns at the same depths and
     // share their halo planes through L2
     const long long grid = std::min<long long>(items, (long long)sms * per_sm);
-    k_step3d<T, TY><<<(unsigned)grid, G::NT, G::SMEM, s>>>(m[0], m[1], m[2], m[3], out, run, zc,
-                                                          derr);
+    if (grav)
+        k_step3d<T, TY, true><<<(unsigned)grid, G::NT, G::SMEM, s>>>(m[0], m[1], m[2], m[3], out,
+                                                                    run, zc, derr);
+    else
+        k_step3d<T, TY, false><<<(unsigned)grid, G::NT, G::SMEM, s>>>(m[0], m[1], m[2], m[3], out,
+                                                                     run, zc, derr);
     return cudaGetLastError();
 }
 

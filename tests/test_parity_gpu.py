@@ -418,3 +418,17 @@ def test_batched_laplace_law_small_drops():
             X, Y = np.meshgrid(np.arange(n), np.arange(n))
             core = np.hypot(X - c, Y - c) < r_eff / 2
             assert mu[core].mean() == pytest.approx(sig / (2 * r_eff), rel=0.1)
+
+
+def test_blow_up_reported_as_unstable_3d():
+    """The 3D kernel leaves blow-up detection to a scan of the fields at the
+    next synchronising call: an unstable no-SAT run is reported there."""
+    rng = np.random.default_rng(1)
+    shape = (16, 16, 32)
+    with acm.Solver(acm.make_params(shape, nu=0.0, sat_mask=0, precision=acm.FP32_DEV)) as s:
+        s.set_fields(1 + 0.1 * rng.standard_normal(shape), *(0.3 * rng.standard_normal(shape)
+                                                               for _ in range(3)))
+        s.step(3000)
+        with pytest.raises(acm.AcmError) as e:
+            s.sync()
+        assert e.value.status == acm.EUNSTABLE
