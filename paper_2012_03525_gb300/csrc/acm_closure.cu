@@ -550,7 +550,7 @@ acm_status acm_closure_create(int nx, int ny, int batch, acm_closure **out)
     c->nparam = n_params();
     const size_t HW = (size_t)nx * ny, NB = HW * batch;
     const int tiles_img = (nx / CTW) * (ny / CTH);
-    c->wg_tiles = 16;
+    c->wg_tiles = 4;  // pixel tiles per weight-gradient CTA (enough CTAs to fill the GPU)
     c->wg_ctas = (tiles_img + c->wg_tiles - 1) / c->wg_tiles;
     c->loss_blocks = 512;
     cudaError_t e = cudaSuccess;

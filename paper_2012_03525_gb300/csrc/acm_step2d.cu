@@ -34,28 +34,38 @@ constexpr int RW2 = T2X + 4, RH2 = T2Y + 4, A2 = RW2 * RH2;
 constexpr int RW3 = T2X + 6, RH3 = T2Y + 6, A3 = RW3 * RH3;
 constexpr int RW4 = T2X + 8, RH4 = T2Y + 8, A4 = RW4 * RH4;
 
+constexpr int NWARP = T2THREADS / 32;
+
+// grid index of window column/row c (may lie up to 4 nodes outside the grid):
+// periodic directions wrap, wall directions clamp (those values are unused)
 __device__ __forceinline__ int wrap_or_clamp(int c, int n, bool periodic)
 {
     if (periodic) {
-        while (c < 0) c += n;
-        while (c >= n) c -= n;
+        if (c < 0) c += n;
+        else if (c >= n) c -= n;
+        if ((unsigned)c >= (unsigned)n) {  // grids narrower than the halo
+            c %= n;
+            if (c < 0) c += n;
+        }
         return c;
     }
     return c < 0 ? 0 : (c >= n ? n - 1 : c);
 }
 
-// Stage a (T2X + 2H) x (T2Y + 2H) window whose first element is node
-// (x0 - H, y0 - H).  Wall directions clamp (those halo values are never used).
-template <typename T, int H>
-__device__ __forceinline__ void stage(T *dst, const T *__restrict__ src, int x0, int y0, int nx,
-                                      int ny, bool perx, bool pery)
+// Visit a (RW x RH) window row by row: warp w takes rows w, w + 8, ...; a
+// lane takes columns lane and lane + 32.  Consecutive lanes touch
+// consecutive shared-memory words (no bank conflicts) and the row index is
+// computed once per row.
+template <int RW, int RH, typename F>
+__device__ __forceinline__ void for_window(F f)
 {
-    constexpr int RW = T2X + 2 * H, RH = T2Y + 2 * H;
-    for (int i = threadIdx.x; i < RW * RH; i += T2THREADS) {
-        int ly = i / RW, lx = i - ly * RW;
-        int gx = wrap_or_clamp(x0 - H + lx, nx, perx);
-        int gy = wrap_or_clamp(y0 - H + ly, ny, pery);
-        dst[i] = src[(long long)gy * nx + gx];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int ly = warp; ly < RH; ly += NWARP) {
+#pragma unroll
+        for (int lx0 = 0; lx0 < RW; lx0 += 32) {
+            const int lx = lx0 + lane;
+            if (lx < RW) f(ly, lx);
+        }
     }
 }
 
@@ -105,7 +115,8 @@ __global__ void __launch_bounds__(T2THREADS)
     T *smu = sphi + A4;
     T *sphs = smu + A3;
     T *smus = sphs + A2;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31;
+    bool nonfinite = false;
 
     for (int item = blockIdx.x; item < nwork; item += gridDim.x) {
         const int4 wk = work[item];
@@ -118,28 +129,46 @@ __global__ void __launch_bounds__(T2THREADS)
         const T rho0 = C[C_RHO0], dt = C[C_DT], nudt = C[C_NUDT], satc = C[C_SATC];
         const T cs2 = C[C_CS2];
         const long long off = R.off;
+        const T *gr = in.f[F_R] + off, *gu = in.f[F_U] + off, *gv = in.f[F_V] + off;
 
         __syncthreads();  // shared memory of the previous item is free
-        stage<T, 2>(sr, in.f[F_R] + off, x0, y0, nx, ny, perx, pery);
-        stage<T, 2>(su, in.f[F_U] + off, x0, y0, nx, ny, perx, pery);
-        stage<T, 2>(sv, in.f[F_V] + off, x0, y0, nx, ny, perx, pery);
-        if (TP) stage<T, 4>(sphi, in.f[F_PHI] + off, x0, y0, nx, ny, perx, pery);
+        {
+            // window columns of this lane (halo 2: rho', u, v; halo 4: phi)
+            const int c2a = wrap_or_clamp(x0 - 2 + lane, nx, perx);
+            const int c2b = wrap_or_clamp(x0 - 2 + lane + 32, nx, perx);
+            for_window<RW2, RH2>([&](int ly, int lx) {
+                const long long row = (long long)wrap_or_clamp(y0 - 2 + ly, ny, pery) * nx;
+                const long long k = row + (lx < 32 ? c2a : c2b);
+                const int i = ly * RW2 + lx;
+                sr[i] = gr[k];
+                su[i] = gu[k];
+                sv[i] = gv[k];
+            });
+            if (TP) {
+                const T *gp = in.f[F_PHI] + off;
+                const int c4a = wrap_or_clamp(x0 - 4 + lane, nx, perx);
+                const int c4b = wrap_or_clamp(x0 - 4 + lane + 32, nx, perx);
+                for_window<RW4, RH4>([&](int ly, int lx) {
+                    const long long row = (long long)wrap_or_clamp(y0 - 4 + ly, ny, pery) * nx;
+                    sphi[ly * RW4 + lx] = gp[row + (lx < 32 ? c4a : c4b)];
+                });
+            }
+        }
         __syncthreads();
 
         const T a = C[C_A], kappa = C[C_KAPPA], mob = C[C_M];
         if (TP) {
             // mu^n on the tile grown by 3 (window origin x0-3)
-            for (int i = tid; i < A3; i += T2THREADS) {
-                int ly = i / RW3, lx = i - ly * RW3;
-                int c4 = (ly + 1) * RW4 + (lx + 1);
-                T f = sphi[c4];
-                smu[i] = T(4) * a * f * (f * f - T(1)) - kappa * lap_iso<T, RW4>(sphi, c4);
-            }
+            for_window<RW3, RH3>([&](int ly, int lx) {
+                const int c4 = (ly + 1) * RW4 + (lx + 1);
+                const T f = sphi[c4];
+                smu[ly * RW3 + lx] =
+                    T(4) * a * f * (f * f - T(1)) - kappa * lap_iso<T, RW4>(sphi, c4);
+            });
         }
         // Eq. (2.10): Delta rho on the tile grown by 1 (interior nodes)
-        for (int i = tid; i < A1; i += T2THREADS) {
-            int ly = i / RW1, lx = i - ly * RW1;
-            int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
+        for_window<RW1, RH1>([&](int ly, int lx) {
+            const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
             bool active = true;
             if (!perx && (gx <= 0 || gx >= nx - 1)) active = false;
             if (!pery && (gy <= 0 || gy >= ny - 1)) active = false;
@@ -153,8 +182,8 @@ __global__ void __launch_bounds__(T2THREADS)
                 d = -dt * (T(0.5) * (mxE - mxW) + T(0.5) * (myN - myS));
                 d += satc * (sr[c + 1] + sr[c - 1] + sr[c + RW2] + sr[c - RW2] - T(4) * sr[c]);
             }
-            sdr[i] = d;
-        }
+            sdr[ly * RW1 + lx] = d;
+        });
         if (!perx || !pery) {
             // wall density: rho_w^{n+1} = (4 rho_1^{n+1} - rho_2^{n+1}) / 3, x faces
             // first, then y faces (corners end with the y extrapolation)
@@ -181,31 +210,30 @@ __global__ void __launch_bounds__(T2THREADS)
         __syncthreads();
         if (TP) {
             // first Heun stage phi* on the tile grown by 2
-            for (int i = tid; i < A2; i += T2THREADS) {
-                int ly = i / RW2, lx = i - ly * RW2;
-                int c4 = (ly + 2) * RW4 + (lx + 2);
-                int c3 = (ly + 1) * RW3 + (lx + 1);
-                T adv = su[i] * gx_iso<T, RW4>(sphi, c4) + sv[i] * gy_iso<T, RW4>(sphi, c4);
+            for_window<RW2, RH2>([&](int ly, int lx) {
+                const int i = ly * RW2 + lx;
+                const int c4 = (ly + 2) * RW4 + (lx + 2);
+                const int c3 = (ly + 1) * RW3 + (lx + 1);
+                const T adv = su[i] * gx_iso<T, RW4>(sphi, c4) + sv[i] * gy_iso<T, RW4>(sphi, c4);
                 sphs[i] = sphi[c4] + dt * (-adv + mob * lap_iso<T, RW3>(smu, c3));
-            }
+            });
             __syncthreads();
             // mu* on the tile grown by 1
-            for (int i = tid; i < A1; i += T2THREADS) {
-                int ly = i / RW1, lx = i - ly * RW1;
-                int c2 = (ly + 1) * RW2 + (lx + 1);
-                T f = sphs[c2];
-                smus[i] = T(4) * a * f * (f * f - T(1)) - kappa * lap_iso<T, RW2>(sphs, c2);
-            }
+            for_window<RW1, RH1>([&](int ly, int lx) {
+                const int c2 = (ly + 1) * RW2 + (lx + 1);
+                const T f = sphs[c2];
+                smus[ly * RW1 + lx] =
+                    T(4) * a * f * (f * f - T(1)) - kappa * lap_iso<T, RW2>(sphs, c2);
+            });
             __syncthreads();
         }
 
         // Eq. (2.11) on the tile interior; write the new state
         const T satm = C[C_SATM];
         const T gxb = C[C_GX], gyb = C[C_GY];
-        for (int i = tid; i < T2X * T2Y; i += T2THREADS) {
-            int ly = i / T2X, lx = i - ly * T2X;
-            int gx = x0 + lx, gy = y0 + ly;
-            if (gx >= nx || gy >= ny) continue;
+        for_window<T2X, T2Y>([&](int ly, int lx) {
+            const int gx = x0 + lx, gy = y0 + ly;
+            if (gx >= nx || gy >= ny) return;
             const int c = (ly + 2) * RW2 + (lx + 2);
             const int c1 = (ly + 1) * RW1 + (lx + 1);
             const T r0 = sr[c], u0 = su[c], v0 = sv[c], d0 = sdr[c1];
@@ -256,7 +284,7 @@ __global__ void __launch_bounds__(T2THREADS)
             out.f[F_R][gi] = rn;
             out.f[F_U][gi] = un;
             out.f[F_V][gi] = vn;
-            bool nonfinite = bad(rn) || bad(un) || bad(vn);
+            T chk = rn + un + vn;
             if (TP) {
                 const int c4 = (ly + 4) * RW4 + (lx + 4);
                 const int c2 = (ly + 2) * RW2 + (lx + 2);
@@ -264,11 +292,12 @@ __global__ void __launch_bounds__(T2THREADS)
                 const T r2 = -adv + mob * lap_iso<T, RW1>(smus, c1);
                 const T phn = T(0.5) * (sphi[c4] + sphs[c2] + dt * r2);
                 out.f[F_PHI][gi] = phn;
-                nonfinite |= bad(phn);
+                chk += phn;
             }
-            if (nonfinite) atomicOr(err, ERR_NONFINITE);
-        }
+            nonfinite |= bad(chk);
+        });
     }
+    if (nonfinite) atomicOr(err, ERR_NONFINITE);
 }
 
 template <typename T, bool TP>
