@@ -370,6 +370,47 @@ def run_closure(args):
     return 0
 
 
+def run_dpsl(args):
+    """The paper's doubly periodic shear layer (Section 3.3: N_L = 320,
+    N_t = 16000, Re = 1e4, 0 <= t <= 1) timed end to end on the GPU in FP64
+    and FP32, next to the paper's own wall time (258.6 s, unnamed CPU)."""
+    import numpy as np
+    import torch
+    from paper_2012_03525_gb300 import acm, build
+    from paper_2012_03525_gb300 import workloads as wl
+    build.build()
+    n, nt = 320, 16000
+    us, nu = wl.dpsl_lattice(n, nt)
+    rho, u, v = wl.dpsl(n)
+    out = {}
+    for name, prec in (("fp64", acm.FP64), ("fp32", acm.FP32_DEV)):
+        s = acm.Solver(acm.make_params((n, n), nu=nu, precision=prec))
+        s.set_fields(rho, u * us, v * us)
+        s.step(64)
+        s.sync()
+        s.set_fields(rho, u * us, v * us)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.step(nt)
+        f = s.fields()
+        secs = time.perf_counter() - t0
+        w = (np.roll(f[2], -1, 1) - np.roll(f[2], 1, 1) - np.roll(f[1], -1, 0) + np.roll(f[1], 1, 0))
+        w = w * 0.5 * n / us
+        out[name] = {"seconds": secs, "GLUPS": n * n * nt / secs / 1e9,
+                     "enstrophy_t1": float(0.5 * (w * w).mean()),
+                     "energy_t1": float(0.5 * ((f[1] / us) ** 2 + (f[2] / us) ** 2).mean())}
+        s.close()
+    print(json.dumps({
+        "metric": "wall time of the DPSL run (t = 0..1)", "value": out["fp64"]["seconds"],
+        "unit": "s", "n_gpus": 1, "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "doubly periodic shear layer 320^2, 16000 steps, Re=1e4 "
+                               "(Section 3.3), one handle, graph-replayed steps, fields read back"},
+        "runs": out,
+        "paper_context": {"seconds": 258.6, "hardware": "unnamed CPU (paper, Section 3.3)"},
+    }))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -377,7 +418,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="tgv3d", choices=["tgv3d", "drops", "closure"],
+    ap.add_argument("--workload", default="tgv3d", choices=["tgv3d", "drops", "closure", "dpsl"],
                     help="tgv3d: the bench line; drops: the batched two-phase workload; "
                          "closure: the learned closure's time-to-eps comparison")
     ap.add_argument("--train-trajectories", type=int, default=32)
@@ -399,6 +440,8 @@ def main():
         return run_batched_drops(args)
     if args.workload == "closure":
         return run_closure(args)
+    if args.workload == "dpsl":
+        return run_dpsl(args)
 
     import numpy as np
     import torch

@@ -145,3 +145,24 @@ def turbulence2d(n: int, seed: int, u_rms: float = 0.05, k0: float = 8.0):
     v = np.real(np.fft.ifft2(-1j * kxs * psi_hat))
     s = u_rms / np.sqrt(np.mean(u * u + v * v))
     return np.ones((n, n)), u * s, v * s
+
+
+def dpsl(n: int, delta_w: float = 80.0, delta_p: float = 0.05):
+    """Doubly periodic shear layer on the unit square (Section 3.3, Eqs.
+    3.3a-c), n nodes per side at x_i = i / n:
+      rho = 1, u = tanh(delta_w (y - 1/4)) for y <= 1/2,
+               tanh(delta_w (3/4 - y)) for y > 1/2,
+      v = delta_p sin(2 pi (x + 1/4)).
+    Velocities in units of the characteristic velocity U = 1."""
+    x = np.arange(n, dtype=np.float64) / n
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    u = np.where(Y <= 0.5, np.tanh(delta_w * (Y - 0.25)), np.tanh(delta_w * (0.75 - Y)))
+    v = delta_p * np.sin(2 * np.pi * (X + 0.25))
+    return np.ones((n, n)), u, v
+
+
+def dpsl_lattice(n: int, nt: int = 16000, re: float = 1e4):
+    """Lattice parameters of the DPSL run with n nodes over L = 1 and nt steps
+    per unit time: (velocity scale u_lat per unit U, nu_lat)."""
+    dx, dt = 1.0 / n, 1.0 / nt
+    return dt / dx, (1.0 / re) * dt / dx ** 2
