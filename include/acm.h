@@ -86,11 +86,14 @@ typedef struct {
     int sat_mask;       /* bit0: continuity SAT of Eq. (2.10), bit1: momentum
                            SAT of Eq. (2.11); 3 = the paper's scheme, other
                            values reproduce the ablation of Section 3.1 */
+    double theta_deg;   /* two-phase contact angle of wall faces (degrees):
+                           d_n phi = -(2/W) cos(theta) (1 - phi_w^2), d_n mu = 0
+                           (Section 2); 90 = neutral wetting */
 } acm_params;
 
 /* Supported combinations (others return ACM_EINVAL):
- *   dim 2: periodic, wall or lid faces; single- or two-phase (two-phase
- *          requires periodic faces); FP64 or FP32_DEV;
+ *   dim 2: periodic, wall or lid faces; single- or two-phase (walls of
+ *          two-phase runs carry the wetting condition); FP64 or FP32_DEV;
  *   dim 3: periodic faces, single-phase; FP64 or FP32_DEV.            */
 
 /* Create a solver for ONE grid.  Validates the parameters, allocates the

@@ -25,6 +25,8 @@
  *     extrapolation (4 rho_1 - rho_2)/3, applied to rho^{n+1} before the
  *     momentum update so that d_alpha rho^{n+1} next to a wall uses it;
  *     corner/edge nodes shared by a stationary wall and a lid are stationary,
+ *   - two-phase walls: ghost nodes mirror the first interior node (zero normal
+ *     derivative of mu) plus the wetting correction for phi (Section 2);
  *   - two-phase: "second order isotropic" operators are the lattice-weighted
  *     D2Q9 (2D) / D3Q19 (3D) gradient and Laplacian; the Cahn-Hilliard
  *     equation (Eq. 2.14) is advanced by Heun's two-stage RK2 with u^n frozen;
@@ -51,6 +53,7 @@ typedef struct {
     int two_phase;         /* 0 or 1 */
     double sigma, W, M;    /* surface tension, interface width, mobility */
     int sat_mask;          /* bit0: continuity SAT, bit1: momentum SAT */
+    double theta_deg;      /* contact angle of wall faces (two-phase) */
 } oracle_params;
 
 typedef struct {
@@ -146,8 +149,45 @@ static const vel_t *vset(const grid_t *G, int *q)
     return D3Q19;
 }
 
+/* Value of a two-phase field at node (i,j,k), where a coordinate may lie one
+   node beyond a wall face.  Wall faces carry the boundary conditions of the
+   two-phase paragraph of Section 2: the ghost node beyond a wall mirrors the
+   node one inside, f(-1) = f(1) (zero normal derivative, used for mu), and
+   for the order parameter the wetting condition d_n phi = -(2/W) cos(theta)
+   (1 - phi_w^2), with n the wall normal pointing into the fluid and the
+   centred difference d_n phi = (phi(1) - phi(-1)) / 2, gives
+   phi(-1) = phi(1) + 2 (2/W) cos(theta) (1 - phi_w^2). */
+enum { F_MIRROR = 0, F_WETTING = 1 };
+
+static double field_at(const grid_t *G, const double *f, int kind, int i, int j, int k)
+{
+    int c[3] = {i, j, k};
+    double add = 0.0;
+    for (int d = 0; d < G->p->dim; ++d) {
+        if (G->periodic[d]) continue;
+        int mirror;
+        if (c[d] == -1) mirror = 1;
+        else if (c[d] == G->n[d]) mirror = G->n[d] - 2;
+        else continue;
+        if (kind == F_WETTING) {
+            /* phi_w: the boundary node nearest the ghost node (the ghost's
+               own coordinates clamped into the box in every walled
+               direction), so that at an edge or corner every wall's term
+               takes the same edge/corner node */
+            int cw[3] = {i, j, k};
+            for (int e = 0; e < G->p->dim; ++e)
+                if (!G->periodic[e]) cw[e] = cw[e] < 0 ? 0 : (cw[e] >= G->n[e] ? G->n[e] - 1 : cw[e]);
+            double pw = f[gidx(G, cw[0], cw[1], cw[2])];
+            double ct = cos(G->p->theta_deg * 3.14159265358979323846 / 180.0);
+            add += 2.0 * (2.0 / G->p->W) * ct * (1.0 - pw * pw);
+        }
+        c[d] = mirror;
+    }
+    return f[gidx(G, c[0], c[1], c[2])] + add;
+}
+
 /* G_iso,d f = (1/c_sL^2) sum_i w_i e_id f(x + e_i) */
-static double grad_iso(const grid_t *G, const double *f, int i, int j, int k, int d)
+static double grad_iso(const grid_t *G, const double *f, int kind, int i, int j, int k, int d)
 {
     int q;
     const vel_t *V = vset(G, &q);
@@ -155,20 +195,20 @@ static double grad_iso(const grid_t *G, const double *f, int i, int j, int k, in
     for (int a = 0; a < q; ++a) {
         if (V[a].e[d] == 0) continue;
         s += V[a].w * V[a].e[d] *
-             f[gidx(G, i + V[a].e[0], j + V[a].e[1], k + V[a].e[2])];
+             field_at(G, f, kind, i + V[a].e[0], j + V[a].e[1], k + V[a].e[2]);
     }
     return s / CS2_LAT;
 }
 
 /* L_iso f = (2/c_sL^2) sum_i w_i (f(x + e_i) - f(x)) */
-static double lap_iso(const grid_t *G, const double *f, int i, int j, int k)
+static double lap_iso(const grid_t *G, const double *f, int kind, int i, int j, int k)
 {
     int q;
     const vel_t *V = vset(G, &q);
     double f0 = f[gidx(G, i, j, k)];
     double s = 0.0;
     for (int a = 1; a < q; ++a)
-        s += V[a].w * (f[gidx(G, i + V[a].e[0], j + V[a].e[1], k + V[a].e[2])] - f0);
+        s += V[a].w * (field_at(G, f, kind, i + V[a].e[0], j + V[a].e[1], k + V[a].e[2]) - f0);
     return 2.0 * s / CS2_LAT;
 }
 
@@ -184,7 +224,7 @@ static void chem_pot(const grid_t *G, const double *phi, double *mu)
             for (int i = 0; i < G->n[0]; ++i) {
                 long c = gidx(G, i, j, k);
                 double f = phi[c];
-                mu[c] = 4.0 * a * f * (f * f - 1.0) - kappa * lap_iso(G, phi, i, j, k);
+                mu[c] = 4.0 * a * f * (f * f - 1.0) - kappa * lap_iso(G, phi, F_WETTING, i, j, k);
             }
 }
 
@@ -200,8 +240,8 @@ static void che_rhs(const grid_t *G, const double *phi, const double *mu,
                 long c = gidx(G, i, j, k);
                 double adv = 0.0;
                 for (int d = 0; d < p->dim; ++d)
-                    adv += uvw[d][c] * grad_iso(G, phi, i, j, k, d);
-                R[c] = -adv + p->M * lap_iso(G, mu, i, j, k);
+                    adv += uvw[d][c] * grad_iso(G, phi, F_WETTING, i, j, k, d);
+                R[c] = -adv + p->M * lap_iso(G, mu, F_MIRROR, i, j, k);
             }
 }
 
@@ -218,10 +258,6 @@ static int setup_grid(const oracle_params *p, grid_t *G)
         if ((lo == OR_PERIODIC) != (hi == OR_PERIODIC)) return -1;
         G->periodic[d] = (lo == OR_PERIODIC);
         if (G->n[d] < (G->periodic[d] ? 1 : 3)) return -1;
-    }
-    if (p->two_phase) {
-        for (int d = 0; d < p->dim; ++d)
-            if (!G->periodic[d]) return -1; /* two-phase walls not in this oracle */
     }
     return 0;
 }
@@ -330,7 +366,7 @@ int oracle_step(const oracle_params *p, double *rho, double *u, double *v,
                                   (dcen(rho1, &nb, a) - dcen(rho, &nb, a));
                         mn += dt * rho1[c0] * p->g[a];
                         if (p->two_phase)
-                            mn += dt * (-phi[c0] * grad_iso(&G, mu, i, j, k, a));
+                            mn += dt * (-phi[c0] * grad_iso(&G, mu, F_MIRROR, i, j, k, a));
                         mnew[a][c0] = mn;
                     }
                 }
@@ -394,8 +430,8 @@ int oracle_grad_lap_iso(const oracle_params *p, const double *f, int d,
         for (int j = 0; j < G.n[1]; ++j)
             for (int i = 0; i < G.n[0]; ++i) {
                 long c = gidx(&G, i, j, k);
-                if (grad) grad[c] = grad_iso(&G, f, i, j, k, d);
-                if (lapl) lapl[c] = lap_iso(&G, f, i, j, k);
+                if (grad) grad[c] = grad_iso(&G, f, F_MIRROR, i, j, k, d);
+                if (lapl) lapl[c] = lap_iso(&G, f, F_MIRROR, i, j, k);
             }
     return 0;
 }

@@ -32,6 +32,7 @@ class OracleParams(ctypes.Structure):
         ("two_phase", ctypes.c_int),
         ("sigma", ctypes.c_double), ("W", ctypes.c_double), ("M", ctypes.c_double),
         ("sat_mask", ctypes.c_int),
+        ("theta_deg", ctypes.c_double),
     ]
 
 
@@ -68,7 +69,8 @@ def _load():
 
 
 def make_params(shape, dt=1.0, nu=0.01, rho0=1.0, bc=None, lid_u=(0, 0, 0), g=(0, 0, 0),
-                two_phase=False, sigma=0.0, W=4.0, M=0.0, sat_mask=3) -> OracleParams:
+                two_phase=False, sigma=0.0, W=4.0, M=0.0, sat_mask=3,
+                theta_deg=90.0) -> OracleParams:
     """``shape`` is (ny, nx) for 2D or (nz, ny, nx) for 3D (array order)."""
     p = OracleParams()
     if len(shape) == 2:
@@ -85,6 +87,7 @@ def make_params(shape, dt=1.0, nu=0.01, rho0=1.0, bc=None, lid_u=(0, 0, 0), g=(0
     p.two_phase = int(bool(two_phase))
     p.sigma, p.W, p.M = sigma, W, M
     p.sat_mask = sat_mask
+    p.theta_deg = theta_deg
     return p
 
 

@@ -44,6 +44,7 @@ class Params(ctypes.Structure):
         ("two_phase", ctypes.c_int),
         ("sigma", ctypes.c_double), ("W", ctypes.c_double), ("M", ctypes.c_double),
         ("precision", ctypes.c_int), ("sat_mask", ctypes.c_int),
+        ("theta_deg", ctypes.c_double),
     ]
 
 
@@ -113,7 +114,8 @@ def load():
 
 
 def make_params(shape, dt=1.0, nu=0.01, rho0=1.0, bc=None, lid_u=(0, 0, 0), g=(0, 0, 0),
-                two_phase=False, sigma=0.0, W=4.0, M=0.0, precision=FP64, sat_mask=3) -> Params:
+                two_phase=False, sigma=0.0, W=4.0, M=0.0, precision=FP64, sat_mask=3,
+                theta_deg=90.0) -> Params:
     """``shape`` is (ny, nx) for 2D or (nz, ny, nx) for 3D (array order)."""
     p = Params()
     if len(shape) == 2:
@@ -131,6 +133,7 @@ def make_params(shape, dt=1.0, nu=0.01, rho0=1.0, bc=None, lid_u=(0, 0, 0), g=(0
     p.sigma, p.W, p.M = sigma, W, M
     p.precision = precision
     p.sat_mask = sat_mask
+    p.theta_deg = theta_deg
     return p
 
 

@@ -100,9 +100,8 @@ acm_status validate(const acm_params &p, std::string &why)
         if (p.two_phase) return bad("two-phase runs are 2D only");
     }
     if (p.two_phase) {
-        for (int f = 0; f < 4; ++f)
-            if (p.bc[f] != ACM_BC_PERIODIC) return bad("two-phase runs need periodic faces");
         if (!(p.W > 0) || !(p.sigma >= 0) || !(p.M >= 0)) return bad("bad sigma/W/M");
+        if (!std::isfinite(p.theta_deg)) return bad("non-finite contact angle");
     }
     for (int d = 0; d < 3; ++d)
         if (!std::isfinite(p.g[d]) || !std::isfinite(p.lid_u[d])) return bad("non-finite g/lid");
@@ -148,6 +147,7 @@ RunDesc describe(const acm_params &p)
     c[C_A] = r.a;
     c[C_KAPPA] = r.kappa;
     c[C_M] = r.M;
+    c[C_WET] = 2.0 * (2.0 / p.W) * std::cos(p.theta_deg * 3.14159265358979323846 / 180.0);
     for (int k = 0; k < NCOEF; ++k) {
         r.cd[k] = c[k];
         r.cf[k] = (float)c[k];

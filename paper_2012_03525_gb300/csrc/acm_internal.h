@@ -33,6 +33,7 @@ enum {
     C_NUDT,   // nu dt
     C_GX, C_GY, C_GZ, C_LIDX, C_LIDY, C_LIDZ,
     C_A, C_KAPPA, C_M,
+    C_WET,    // 2 (2/W) cos(theta): wetting term of the ghost order parameter
     NCOEF
 };
 

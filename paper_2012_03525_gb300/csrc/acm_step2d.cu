@@ -95,6 +95,48 @@ __device__ __forceinline__ T gy_iso(const T *f, int c)
            T(1.0 / 12.0) * (f[c + RW + 1] + f[c + RW - 1] - f[c - RW + 1] - f[c - RW - 1]);
 }
 
+// Two-phase wall boundary conditions on a window of the tile (halo H) whose
+// first element is node (x0 - H, y0 - H): the ghost node one beyond a wall
+// face takes the value of the node one inside the wall (zero normal
+// derivative, for mu) plus, for the order parameter (wet != 0), the wetting
+// term wet (1 - f_w^2) with f_w the wall node (Section 2: d_n phi =
+// -(2/W) cos(theta) (1 - phi_w^2), centred difference).  A corner ghost is
+// mirrored through both walls and takes both walls' terms, each evaluated at
+// the corner node.  x faces first, then y faces (which overwrite the
+// corners); deeper ghost nodes are never read.
+template <typename T, int RW, int RH, int H>
+__device__ __forceinline__ void wall_ghosts(T *f, int x0, int y0, int nx, int ny, bool perx,
+                                            bool pery, T wet)
+{
+    if (!perx) {
+        for_window<RW, RH>([&](int ly, int lx) {
+            const int gx = x0 - H + lx;
+            if (gx != -1 && gx != nx) return;
+            const int s = gx == -1 ? 1 : -1;
+            const T fw = f[ly * RW + lx + s];
+            f[ly * RW + lx] = f[ly * RW + lx + 2 * s] + wet * (T(1) - fw * fw);
+        });
+        __syncthreads();
+    }
+    if (!pery) {
+        for_window<RW, RH>([&](int ly, int lx) {
+            const int gy = y0 - H + ly;
+            if (gy != -1 && gy != ny) return;
+            const int gx = x0 - H + lx;
+            const int s = gy == -1 ? RW : -RW;
+            if (!perx && (gx == -1 || gx == nx)) {
+                const int t = s + (gx == -1 ? 1 : -1);
+                const T fw = f[ly * RW + lx + t];
+                f[ly * RW + lx] = f[ly * RW + lx + 2 * t] + T(2) * wet * (T(1) - fw * fw);
+                return;
+            }
+            const T fw = f[ly * RW + lx + s];
+            f[ly * RW + lx] = f[ly * RW + lx + 2 * s] + wet * (T(1) - fw * fw);
+        });
+        __syncthreads();
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ bool bad(T x)
 {
@@ -157,6 +199,9 @@ __global__ void __launch_bounds__(T2THREADS)
         __syncthreads();
 
         const T a = C[C_A], kappa = C[C_KAPPA], mob = C[C_M];
+        const bool walls = !perx || !pery;
+        if (TP && walls)
+            wall_ghosts<T, RW4, RH4, 4>(sphi, x0, y0, nx, ny, perx, pery, C[C_WET]);
         if (TP) {
             // mu^n on the tile grown by 3 (window origin x0-3)
             for_window<RW3, RH3>([&](int ly, int lx) {
@@ -208,6 +253,7 @@ __global__ void __launch_bounds__(T2THREADS)
             }
         }
         __syncthreads();
+        if (TP && walls) wall_ghosts<T, RW3, RH3, 3>(smu, x0, y0, nx, ny, perx, pery, T(0));
         if (TP) {
             // first Heun stage phi* on the tile grown by 2
             for_window<RW2, RH2>([&](int ly, int lx) {
@@ -218,6 +264,7 @@ __global__ void __launch_bounds__(T2THREADS)
                 sphs[i] = sphi[c4] + dt * (-adv + mob * lap_iso<T, RW3>(smu, c3));
             });
             __syncthreads();
+            if (walls) wall_ghosts<T, RW2, RH2, 2>(sphs, x0, y0, nx, ny, perx, pery, C[C_WET]);
             // mu* on the tile grown by 1
             for_window<RW1, RH1>([&](int ly, int lx) {
                 const int c2 = (ly + 1) * RW2 + (lx + 1);
@@ -226,6 +273,7 @@ __global__ void __launch_bounds__(T2THREADS)
                     T(4) * a * f * (f * f - T(1)) - kappa * lap_iso<T, RW2>(sphs, c2);
             });
             __syncthreads();
+            if (walls) wall_ghosts<T, RW1, RH1, 1>(smus, x0, y0, nx, ny, perx, pery, T(0));
         }
 
         // Eq. (2.11) on the tile interior; write the new state

@@ -166,3 +166,74 @@ def dpsl_lattice(n: int, nt: int = 16000, re: float = 1e4):
     per unit time: (velocity scale u_lat per unit U, nu_lat)."""
     dx, dt = 1.0 / n, 1.0 / nt
     return dt / dx, (1.0 / re) * dt / dx ** 2
+
+
+@dataclasses.dataclass
+class CapillaryWave:
+    """Lattice parameters of the 2D capillary wave (Section 3.4): unit square,
+    N_L nodes per side length L, N_t = c N_L steps per T_c = L / U_c with the
+    capillary velocity U_c = sigma / (rho0 nu); Re = sigma L / (rho0 nu^2),
+    Cn = W / L, Pe = U_c L^2 / (M sigma).  In lattice units (delta_x =
+    delta_t = 1): U_c = 1 / c, nu = U_c N_L / Re, sigma = U_c nu,
+    W = Cn N_L, M = U_c N_L^2 / (Pe sigma).  The grid is N_L periodic columns
+    by N_L + 1 rows, the first and last rows being the no-slip walls."""
+    n_l: int
+    c: float
+    re: float
+    cn: float
+    pe: float = 2e4
+    amp: float = 0.01
+
+    @property
+    def u_c(self):
+        return 1.0 / self.c
+
+    @property
+    def nu(self):
+        return self.u_c * self.n_l / self.re
+
+    @property
+    def sigma(self):
+        return self.u_c * self.nu
+
+    @property
+    def W(self):
+        return self.cn * self.n_l
+
+    @property
+    def M(self):
+        return self.u_c * self.n_l ** 2 / (self.pe * self.sigma)
+
+    @property
+    def steps_per_tc(self):
+        return self.c * self.n_l
+
+    @property
+    def shape(self):
+        return (self.n_l + 1, self.n_l)
+
+    def initial(self):
+        """phi = tanh(2 (y - h(x)) / W), h(x) = L/2 + A_p L cos(k (x + L/2)),
+        fluid at rest, rho = 1 (phi = +1 in the upper half)."""
+        L = self.n_l
+        x = np.arange(L, dtype=np.float64)
+        y = np.arange(L + 1, dtype=np.float64)
+        X, Y = np.meshgrid(x, y, indexing="xy")
+        h = 0.5 * L + self.amp * L * np.cos(2.0 * np.pi / L * (X + 0.5 * L))
+        phi = np.tanh(2.0 * (Y - h) / self.W)
+        z = np.zeros(self.shape)
+        return np.ones(self.shape), z, z.copy(), phi
+
+
+def wall_cap(nx: int, ny: int, radius: float, theta_deg: float, W: float = 4.0, xc=None):
+    """2D drop sitting on the wall row y = 0 as a circular cap of radius R
+    meeting the wall at the contact angle theta (measured inside the drop,
+    phi = +1): centre at (xc, -R cos theta), phi = -tanh(2 (r - R) / W).
+    Fluid at rest, rho = 1."""
+    xc = (nx - 1) / 2.0 if xc is None else xc
+    yc = -radius * np.cos(np.radians(theta_deg))
+    x = np.arange(nx, dtype=np.float64)
+    y = np.arange(ny, dtype=np.float64)
+    X, Y = np.meshgrid(x, y, indexing="xy")
+    phi = -np.tanh(2.0 * (np.hypot(X - xc, Y - yc) - radius) / W)
+    return np.ones((ny, nx)), np.zeros((ny, nx)), np.zeros((ny, nx)), phi

@@ -53,7 +53,7 @@ def test_params_struct_layout_matches_header():
     (dict(shape=(3, 8), bc=[0, 0, 1, 1, 0, 0]), "walls"),
     (dict(shape=(4, 8, 8), bc=[1, 1, 0, 0, 0, 0]), "3D"),
     (dict(shape=(8, 8), two_phase=True, W=0.0), "sigma/W/M"),
-    (dict(shape=(8, 8), two_phase=True, bc=[1, 1, 0, 0, 0, 0]), "two-phase"),
+    (dict(shape=(8, 8), two_phase=True, theta_deg=float("nan")), "contact angle"),
     (dict(shape=(8, 8), sat_mask=4), "sat_mask"),
     (dict(shape=(8, 8), precision=7), "precision"),
 ])
