@@ -171,6 +171,81 @@ __device__ __forceinline__ void node_update(const T (&r)[7], const T (&u)[7], co
     rn = r[0] + d[0];
 }
 
+// Packed FP32 (two lanes per instruction, sm_100+ FFMA2/FADD2/FMUL2) for the
+// FP32 instantiation: a thread's two nodes (lane x = lower node a, lane y =
+// upper node b) run through the same arithmetic, so every operation of
+// Eq. (2.10) and Eq. (2.11) on the own nodes is issued once for both.  Each
+// lane rounds exactly like the scalar operation it replaces.
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 splat(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// reciprocal of rho^{n+1} = 1 + O(Ma^2): the hardware approximation (1 ulp)
+// suffices, since it only scales the O(Ma^2)-relative increment of u
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// coefficient pairs of the packed update (negated where a term is subtracted)
+struct K2 {
+    float2 rho0, hdt, nhdt, hdtcs2, nhdtcs2, nudt, hsatm, nhsatm, m6, satc, dt, gx, gy, gz;
+};
+
+// Eq. (2.11) for both own nodes; arrays in the order C, E, W, N, S, U, D.
+// Differences are split into a positive and a negative chain so that no
+// operand needs negating: -hdt (P - N) = fma(-hdt, P, hdt N).
+template <bool GRAV>
+__device__ __forceinline__ void node_update2(const float2 (&r)[7], const float2 (&u)[7],
+                                             const float2 (&v)[7], const float2 (&w)[7],
+                                             const float2 (&d)[7], const K2 &K, float2 &rn,
+                                             float2 &un, float2 &vn, float2 &wn)
+{
+    float2 mx[7], my[7], mz[7];
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        const float2 q = add2(K.rho0, r[k]);
+        mx[k] = mul2(q, u[k]);
+        my[k] = mul2(q, v[k]);
+        mz[k] = mul2(q, w[k]);
+    }
+    auto lap = [&](const float2 (&m)[7]) {
+        return fma2(K.m6, m[0], add2(add2(add2(m[1], m[2]), add2(m[3], m[4])), add2(m[5], m[6])));
+    };
+    // R += -hdt * (twice the centred difference of m u_b over b)
+    auto flux = [&](const float2 (&m)[7], float2 R) {
+        const float2 P = fma2(m[1], u[1], fma2(m[3], v[3], mul2(m[5], w[5])));
+        const float2 N = fma2(m[2], u[2], fma2(m[4], v[4], mul2(m[6], w[6])));
+        return fma2(K.nhdt, P, fma2(K.hdt, N, R));
+    };
+    const float2 rho1 = add2(add2(K.rho0, r[0]), d[0]);
+    const float2 inv = f2(rcp_approx(rho1.x), rcp_approx(rho1.y));
+    float2 rx = flux(mx, mul2(K.nudt, lap(mx)));
+    float2 ry = flux(my, mul2(K.nudt, lap(my)));
+    float2 rz = flux(mz, mul2(K.nudt, lap(mz)));
+    rx = fma2(K.nhdtcs2, r[1], fma2(K.hdtcs2, r[2], rx));
+    ry = fma2(K.nhdtcs2, r[3], fma2(K.hdtcs2, r[4], ry));
+    rz = fma2(K.nhdtcs2, r[5], fma2(K.hdtcs2, r[6], rz));
+    rx = fma2(K.nhsatm, d[1], fma2(K.hsatm, d[2], rx));
+    ry = fma2(K.nhsatm, d[3], fma2(K.hsatm, d[4], ry));
+    rz = fma2(K.nhsatm, d[5], fma2(K.hsatm, d[6], rz));
+    if (GRAV) {
+        const float2 fb = mul2(K.dt, rho1);
+        rx = fma2(fb, K.gx, rx);
+        ry = fma2(fb, K.gy, ry);
+        rz = fma2(fb, K.gz, rz);
+    }
+    const float2 nd = f2(-d[0].x, -d[0].y);
+    un = fma2(fma2(nd, u[0], rx), inv, u[0]);
+    vn = fma2(fma2(nd, v[0], ry), inv, v[0]);
+    wn = fma2(fma2(nd, w[0], rz), inv, w[0]);
+    rn = add2(r[0], d[0]);
+}
+
 template <int J>
 using IC = std::integral_constant<int, J>;
 
@@ -227,6 +302,12 @@ __global__ void __launch_bounds__(T3X *TY / 2, Prec<T>::MINB * 16 / TY)
     const T satc = C[C_SATC], hsatm = T(0.5) * C[C_SATM];
     const T gfx = C[C_GX], gfy = C[C_GY], gfz = C[C_GZ];
     constexpr uint32_t TX_BYTES = 4u * G::PLANE * sizeof(T);
+    constexpr bool PACK = std::is_same<T, float>::value;
+    const K2 K{splat((float)rho0),  splat((float)hdt),    splat(-(float)hdt),
+               splat((float)hdtcs2), splat(-(float)hdtcs2), splat((float)nudt),
+               splat((float)hsatm), splat(-(float)hsatm), splat(-6.0f),
+               splat((float)satc),  splat((float)dt),     splat((float)gfx),
+               splat((float)gfy),   splat((float)gfz)};
 
     if (tid == 0) {
         for (int s = 0; s < NSLOT; ++s) mbar_init(&bar[s], 1);
@@ -292,6 +373,25 @@ __global__ void __launch_bounds__(T3X *TY / 2, Prec<T>::MINB * 16 / TY)
     auto delta_rho = [&](int sm, int s0, int sp, T *dw, const Col<T> &Cd, const Col<T> &C0,
                          const Col<T> &Cu, T (&dout)[2]) {
         const T *pr = S + s0 * 4 * PE, *pu = pr + PE, *pv = pr + 2 * PE;
+        if constexpr (PACK) {
+            // both own nodes at once (lane x: node a, whose N is node b;
+            // lane y: node b, whose S is node a)
+            const float2 rE = f2(pr[ca + 1], pr[cb + 1]), rW = f2(pr[ca - 1], pr[cb - 1]);
+            const float2 rN = f2(C0.r[1], pr[cb + RW]), rS = f2(pr[ca - RW], C0.r[0]);
+            const float2 uE = f2(pu[ca + 1], pu[cb + 1]), uW = f2(pu[ca - 1], pu[cb - 1]);
+            const float2 vN = f2(C0.v[1], pv[cb + RW]), vS = f2(pv[ca - RW], C0.v[0]);
+            const float2 rU = f2(Cu.r[0], Cu.r[1]), wU = f2(Cu.w[0], Cu.w[1]);
+            const float2 rD = f2(Cd.r[0], Cd.r[1]), wD = f2(Cd.w[0], Cd.w[1]);
+            const float2 P = fma2(add2(K.rho0, rE), uE,
+                                  fma2(add2(K.rho0, rN), vN, mul2(add2(K.rho0, rU), wU)));
+            const float2 N = fma2(add2(K.rho0, rW), uW,
+                                  fma2(add2(K.rho0, rS), vS, mul2(add2(K.rho0, rD), wD)));
+            const float2 lap = fma2(K.m6, f2(C0.r[0], C0.r[1]),
+                                    add2(add2(add2(rE, rW), add2(rN, rS)), add2(rU, rD)));
+            const float2 dd = fma2(K.satc, lap, fma2(K.nhdt, P, mul2(K.hdt, N)));
+            dout[0] = dd.x;
+            dout[1] = dd.y;
+        } else {
         {   // lower node a: N is node b
             const T rE = pr[ca + 1], rW = pr[ca - 1], rS = pr[ca - RW], rN = C0.r[1];
             const T div = ((rho0 + rE) * pu[ca + 1] - (rho0 + rW) * pu[ca - 1]) +
@@ -307,6 +407,7 @@ __global__ void __launch_bounds__(T3X *TY / 2, Prec<T>::MINB * 16 / TY)
                           ((rho0 + Cu.r[1]) * Cu.w[1] - (rho0 + Cd.r[1]) * Cd.w[1]);
             const T lap = (rE + rW) + (rN + rS) + (Cu.r[1] + Cd.r[1]) - T(6) * C0.r[1];
             dout[1] = satc * lap - hdt * div;
+        }
         }
         dw[da] = dout[0];
         dw[db] = dout[1];
@@ -391,19 +492,49 @@ __global__ void __launch_bounds__(T3X *TY / 2, Prec<T>::MINB * 16 / TY)
             constexpr int SM = (J + 1) % NSLOT, S0 = (J + 2) % NSLOT;  // planes z-1, z
             constexpr int S1 = (J + 3) % NSLOT, S2 = (J + 4) % NSLOT;  // planes z+1, z+2
             const int z = zg + J;
-            __syncthreads();  // plane z-1 and the Delta-rho window of z-1 are free
+            // One barrier per plane: after it, plane z-1 (slot SM) and the
+            // Delta-rho window of z-1 are free, the window of z written in
+            // the previous step is complete, and every wait of the previous
+            // step has returned, so the abort flag reads the same in every
+            // thread.  Plane z and z+1 were waited for by each thread itself.
+            __syncthreads();
+            if (*s_abort) return false;
             if (tid == 0 && z + NSLOT - 1 <= zlast) issue(SM, z + NSLOT - 1, x0, y0);
             wait(S2);
             load_col(S2, Q[S2]);
-            // harmless on stale data if the wait gave up
+            // harmless on stale data if the wait gave up (checked at the next barrier)
             delta_rho(S0, S1, S2, SD + ((z + 1) & 1) * P1, Q[S0], Q[S1], Q[S2], D[S1]);
-            __syncthreads();
-            if (*s_abort) return;
 
             const T *pr = S + S0 * 4 * PE, *pu = pr + PE, *pv = pr + 2 * PE, *pw = pr + 3 * PE;
             const T *dz = SD + (z & 1) * P1;
             const Col<T> &Xm = Q[SM], &X0 = Q[S0], &Xp = Q[S1];
             T ra, ua, va, wa, rb, ub, vb, wb;
+            if constexpr (PACK) {
+                const float2 r[7] = {f2(X0.r[0], X0.r[1]), f2(pr[ca + 1], pr[cb + 1]),
+                                     f2(pr[ca - 1], pr[cb - 1]), f2(X0.r[1], pr[cb + RW]),
+                                     f2(pr[ca - RW], X0.r[0]), f2(Xp.r[0], Xp.r[1]),
+                                     f2(Xm.r[0], Xm.r[1])};
+                const float2 u[7] = {f2(X0.u[0], X0.u[1]), f2(pu[ca + 1], pu[cb + 1]),
+                                     f2(pu[ca - 1], pu[cb - 1]), f2(X0.u[1], pu[cb + RW]),
+                                     f2(pu[ca - RW], X0.u[0]), f2(Xp.u[0], Xp.u[1]),
+                                     f2(Xm.u[0], Xm.u[1])};
+                const float2 v[7] = {f2(X0.v[0], X0.v[1]), f2(pv[ca + 1], pv[cb + 1]),
+                                     f2(pv[ca - 1], pv[cb - 1]), f2(X0.v[1], pv[cb + RW]),
+                                     f2(pv[ca - RW], X0.v[0]), f2(Xp.v[0], Xp.v[1]),
+                                     f2(Xm.v[0], Xm.v[1])};
+                const float2 w[7] = {f2(X0.w[0], X0.w[1]), f2(pw[ca + 1], pw[cb + 1]),
+                                     f2(pw[ca - 1], pw[cb - 1]), f2(X0.w[1], pw[cb + RW]),
+                                     f2(pw[ca - RW], X0.w[0]), f2(Xp.w[0], Xp.w[1]),
+                                     f2(Xm.w[0], Xm.w[1])};
+                const float2 d[7] = {f2(D[S0][0], D[S0][1]), f2(dz[da + 1], dz[db + 1]),
+                                     f2(dz[da - 1], dz[db - 1]), f2(D[S0][1], dz[db + RW1]),
+                                     f2(dz[da - RW1], D[S0][0]), f2(D[S1][0], D[S1][1]),
+                                     f2(D[SM][0], D[SM][1])};
+                float2 rn, un, vn, wn;
+                node_update2<GRAV>(r, u, v, w, d, K, rn, un, vn, wn);
+                ra = rn.x; ua = un.x; va = vn.x; wa = wn.x;
+                rb = rn.y; ub = un.y; vb = vn.y; wb = wn.y;
+            } else {
             {   // lower node a: N neighbour is node b
                 const T r[7] = {X0.r[0], pr[ca + 1], pr[ca - 1], X0.r[1], pr[ca - RW], Xp.r[0], Xm.r[0]};
                 const T u[7] = {X0.u[0], pu[ca + 1], pu[ca - 1], X0.u[1], pu[ca - RW], Xp.u[0], Xm.u[0]};
@@ -422,20 +553,18 @@ __global__ void __launch_bounds__(T3X *TY / 2, Prec<T>::MINB * 16 / TY)
                 node_update<T, GRAV>(r, u, v, w, d, rho0, hdt, hdtcs2, nudt, hsatm, dt, gfx, gfy,
                                      gfz, rb, ub, vb, wb);
             }
+            }
             store2(base_a + (long long)z * PXY, ra, ua, va, wa, rb, ub, vb, wb);
+            return true;
         };
 
         for (int zg = zbeg; zg < zend; zg += NSLOT) {
-            step(IC<0>{}, zg);
-            if (zg + 1 >= zend || *s_abort) break;
-            step(IC<1>{}, zg);
-            if (zg + 2 >= zend || *s_abort) break;
-            step(IC<2>{}, zg);
-            if (zg + 3 >= zend || *s_abort) break;
-            step(IC<3>{}, zg);
+            if (!step(IC<0>{}, zg) || zg + 1 >= zend) break;
+            if (!step(IC<1>{}, zg) || zg + 2 >= zend) break;
+            if (!step(IC<2>{}, zg) || zg + 3 >= zend) break;
+            if (!step(IC<3>{}, zg)) break;
             if (NSLOT > 4) {
-                if (zg + 4 >= zend || *s_abort) break;
-                step(IC<(NSLOT > 4 ? 4 : 0)>{}, zg);
+                if (zg + 4 >= zend || !step(IC<(NSLOT > 4 ? 4 : 0)>{}, zg)) break;
             }
         }
         __syncthreads();  // every read of this chunk's planes is done
