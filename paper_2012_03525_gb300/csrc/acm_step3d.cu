@@ -83,7 +83,10 @@ template <typename T>
 struct Prec;
 template <>
 struct Prec<float> {
-    static constexpr int NSLOT = 5;
+#ifndef ACM_STEP3D_NSLOT
+#define ACM_STEP3D_NSLOT 5
+#endif
+    static constexpr int NSLOT = ACM_STEP3D_NSLOT;
 #ifndef ACM_STEP3D_MINB
 #define ACM_STEP3D_MINB 2
 #endif
@@ -248,6 +251,26 @@ __device__ __forceinline__ void node_update2(const float2 (&r)[7], const float2 
 
 template <int J>
 using IC = std::integral_constant<int, J>;
+
+// z steps J .. N-1 of one pass over the slot ring (slot indices constant in
+// each): stops after plane zend-1 or when a step reports an abort
+template <int J, int N>
+struct Unroll {
+    template <typename F>
+    __device__ __forceinline__ static bool run(F &step, int zg, int zend)
+    {
+        if (!step(IC<J>{}, zg) || zg + J + 1 >= zend) return false;
+        return Unroll<J + 1, N>::run(step, zg, zend);
+    }
+};
+template <int N>
+struct Unroll<N, N> {
+    template <typename F>
+    __device__ __forceinline__ static bool run(F &, int, int)
+    {
+        return true;
+    }
+};
 
 // Write a node's periodic images in the ghost layers (both images exist when
 // the grid is narrower than 2 * T3PAD); only the threads on the first/last
@@ -558,15 +581,8 @@ __global__ void __launch_bounds__(T3X *TY / 2, Prec<T>::MINB * 16 / TY)
             return true;
         };
 
-        for (int zg = zbeg; zg < zend; zg += NSLOT) {
-            if (!step(IC<0>{}, zg) || zg + 1 >= zend) break;
-            if (!step(IC<1>{}, zg) || zg + 2 >= zend) break;
-            if (!step(IC<2>{}, zg) || zg + 3 >= zend) break;
-            if (!step(IC<3>{}, zg)) break;
-            if (NSLOT > 4) {
-                if (zg + 4 >= zend || !step(IC<(NSLOT > 4 ? 4 : 0)>{}, zg)) break;
-            }
-        }
+        for (int zg = zbeg; zg < zend; zg += NSLOT)
+            if (!Unroll<0, NSLOT>::run(step, zg, zend)) break;
         __syncthreads();  // every read of this chunk's planes is done
         if (*s_abort) break;
     }
