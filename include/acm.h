@@ -56,8 +56,11 @@ typedef enum {
     ACM_ESTATE = -6     /* call out of order (e.g. step before set_fields) */
 } acm_status;
 
-/* boundary condition of one face */
-enum { ACM_BC_PERIODIC = 0, ACM_BC_WALL = 1, ACM_BC_LID = 2 };
+/* boundary condition of one face.  ACM_BC_HALO marks the z faces of a 3D
+ * sub-domain: the run is one z-slab of a larger periodic grid, and its two
+ * neighbour planes beyond each z face are ghost planes copied from the
+ * adjacent slabs (see acm_batch_create) */
+enum { ACM_BC_PERIODIC = 0, ACM_BC_WALL = 1, ACM_BC_LID = 2, ACM_BC_HALO = 3 };
 
 /* storage/arithmetic precision of the fields */
 enum {
@@ -94,7 +97,8 @@ typedef struct {
 /* Supported combinations (others return ACM_EINVAL):
  *   dim 2: periodic, wall or lid faces; single- or two-phase (walls of
  *          two-phase runs carry the wetting condition); FP64 or FP32_DEV;
- *   dim 3: periodic faces, single-phase; FP64 or FP32_DEV.            */
+ *   dim 3: periodic faces (x, y; z periodic or ACM_BC_HALO on both z
+ *          faces), single-phase; FP64 or FP32_DEV.                    */
 
 /* Create a solver for ONE grid.  Validates the parameters, allocates the
  * double-buffered device fields on the current CUDA device and returns the
@@ -103,11 +107,22 @@ typedef struct {
  * acm_set_fields. */
 acm_status acm_create(const acm_params *params, acm_handle **out);
 
-/* Create a solver for NRUNS independent grids (a batch).  params[r] describes
- * run r; all runs must share dim (2), precision, two_phase and the boundary
- * kind.  Grid sizes and physical parameters may differ per run.  One
- * acm_step advances every run by one step with one persistent kernel launch
- * over a (run, tile) work list. */
+/* Create a solver for NRUNS grids (a batch).
+ * dim 2: independent runs.  params[r] describes run r; all runs share
+ *   precision and two_phase.  Grid sizes and physical parameters may differ
+ *   per run.  One acm_step advances every run by one step with one
+ *   persistent kernel launch over a (run, tile) work list.
+ * dim 3: sub-domains of ONE periodic grid split along z (the slab
+ *   decomposition a multi-GPU run would use, emulated on one GPU).  Every
+ *   run has ACM_BC_HALO z faces, the same nx, ny and physical parameters;
+ *   run r covers the next nz_r planes, and run r+1 (run 0 after the last)
+ *   is its upper neighbour.  Each run stores two ghost planes beyond each z
+ *   face.  One acm_step first copies, for every pair of neighbours, the two
+ *   boundary planes of each into the ghost planes of the other (one
+ *   halo-copy kernel launch: the exchange step of Eqs. 2.10-2.11, whose
+ *   stencil reaches two planes through Delta rho), then advances each slab
+ *   with its own step kernel launch.  The result is bitwise equal to the
+ *   same grid run as one periodic handle. */
 acm_status acm_batch_create(const acm_params *params, int nruns, acm_handle **out);
 
 /* Use this CUDA stream (a cudaStream_t, may be NULL for the legacy default

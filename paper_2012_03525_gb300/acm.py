@@ -13,7 +13,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libacm.so")
 
 OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5, -6
-BC_PERIODIC, BC_WALL, BC_LID = 0, 1, 2
+BC_PERIODIC, BC_WALL, BC_LID, BC_HALO = 0, 1, 2, 3
 FP64, FP32_DEV = 0, 1
 TUNE_ZCHUNKS, TUNE_T3Y, TUNE_GRAPH_STEPS, TUNE_BLOCKS = 1, 2, 3, 4
 
@@ -135,6 +135,21 @@ def make_params(shape, dt=1.0, nu=0.01, rho0=1.0, bc=None, lid_u=(0, 0, 0), g=(0
     p.sat_mask = sat_mask
     p.theta_deg = theta_deg
     return p
+
+
+def subdomain_params(shape, nz_parts, **kw) -> list:
+    """Parameters of a 3D periodic grid ``shape`` = (nz, ny, nx) split along z
+    into slabs of ``nz_parts`` planes (summing to nz), for
+    ``Solver(list_of_params)``: every slab gets ACM_BC_HALO z faces."""
+    nz, ny, nx = shape
+    if sum(nz_parts) != nz:
+        raise ValueError("slab heights must sum to nz")
+    out = []
+    for n in nz_parts:
+        p = make_params((n, ny, nx), **kw)
+        p.bc[4] = p.bc[5] = BC_HALO
+        out.append(p)
+    return out
 
 
 def _dptr(a):

@@ -36,8 +36,9 @@ struct acm_handle {
     int red_blocks = 0;
     double *dout = nullptr;
     double *dstage = nullptr;
-    CUtensorMap maps[2][4];
+    std::vector<CUtensorMap> maps;  // 3D: [buffer][run][field]
     bool maps_ok = false;
+    bool halo = false;              // 3D sub-domains (ACM_BC_HALO z faces)
     cudaGraphExec_t gexec = nullptr;
     Tuning tune;
     std::string err;
@@ -68,7 +69,10 @@ acm_status cuda_fail(acm_handle *h, cudaError_t e, const char *what)
         if (e_ != cudaSuccess) return cuda_fail((h), e_, #call); \
     } while (0)
 
-bool valid_bc(int b) { return b == ACM_BC_PERIODIC || b == ACM_BC_WALL || b == ACM_BC_LID; }
+bool valid_bc(int b)
+{
+    return b == ACM_BC_PERIODIC || b == ACM_BC_WALL || b == ACM_BC_LID || b == ACM_BC_HALO;
+}
 
 acm_status validate(const acm_params &p, std::string &why)
 {
@@ -89,13 +93,21 @@ acm_status validate(const acm_params &p, std::string &why)
         const int lo = p.bc[2 * d], hi = p.bc[2 * d + 1];
         if (d >= p.dim) continue;
         if (!valid_bc(lo) || !valid_bc(hi)) return bad("unknown boundary kind");
+        if ((lo == ACM_BC_HALO) != (hi == ACM_BC_HALO))
+            return bad("ACM_BC_HALO must be on both faces of an axis");
+        if (lo == ACM_BC_HALO) {
+            if (p.dim != 3 || d != 2) return bad("ACM_BC_HALO is for the z faces of 3D grids");
+            if (n[d] < 2) return bad("sub-domains need nz >= 2");
+            continue;
+        }
         if ((lo == ACM_BC_PERIODIC) != (hi == ACM_BC_PERIODIC))
             return bad("a periodic face must be paired with a periodic face");
         if (lo != ACM_BC_PERIODIC && n[d] < 4) return bad("walls need >= 4 nodes across");
     }
     if (p.dim == 3) {
         for (int f = 0; f < 6; ++f)
-            if (p.bc[f] != ACM_BC_PERIODIC) return bad("3D grids support periodic faces only");
+            if (p.bc[f] != ACM_BC_PERIODIC && !(f >= 4 && p.bc[f] == ACM_BC_HALO))
+                return bad("3D grids support periodic faces only (z: periodic or ACM_BC_HALO)");
         if (p.nx < 2 || p.ny < 2) return bad("3D grids need nx, ny >= 2");
         if (p.two_phase) return bad("two-phase runs are 2D only");
     }
@@ -152,6 +164,7 @@ RunDesc describe(const acm_params &p)
         r.cd[k] = c[k];
         r.cf[k] = (float)c[k];
     }
+    r.zg = (p.dim == 3 && p.bc[4] == ACM_BC_HALO) ? 2 : 0;
     if (p.dim == 3) {
         r.pad = T3PAD;
         r.px = ((p.nx + 2 * T3PAD + 7) / 8) * 8;
@@ -184,22 +197,31 @@ acm_status build_maps(acm_handle *h)
     if (h->dim != 3) return ACM_OK;
     auto fn = encode_fn();
     if (!fn) return fail(h, ACM_ECUDA, "cuTensorMapEncodeTiled is not available");
-    const RunDesc &R = h->runs[0];
     const size_t es = h->esize();
-    cuuint64_t dims[3] = {(cuuint64_t)R.px, (cuuint64_t)R.py, (cuuint64_t)R.nz};
-    cuuint64_t strides[2] = {(cuuint64_t)(R.px * es), (cuuint64_t)(R.px * R.py * es)};
-    cuuint32_t box[3] = {(cuuint32_t)(T3X + 4), (cuuint32_t)(h->tune.t3y + 4), 1};
-    cuuint32_t estr[3] = {1, 1, 1};
+    h->maps.resize((size_t)2 * h->nruns * 4);
     const CUtensorMapDataType dt =
         h->prec == ACM_FP64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-    for (int b = 0; b < 2; ++b)
-        for (int f = 0; f < 4; ++f) {
-            CUresult r = fn(&h->maps[b][f], dt, 3, h->buf[b][f], dims, strides, box, estr,
-                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-            if (r != CUDA_SUCCESS)
-                return fail(h, ACM_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string(r) + ")");
-        }
+    for (int run = 0; run < h->nruns; ++run) {
+        // one map per (buffer, run, field): the run's padded planes, ghost
+        // planes included; base = pool + run offset (a multiple of 32
+        // elements, so 16-byte aligned)
+        const RunDesc &R = h->runs[run];
+        cuuint64_t dims[3] = {(cuuint64_t)R.px, (cuuint64_t)R.py, (cuuint64_t)(R.nz + 2 * R.zg)};
+        cuuint64_t strides[2] = {(cuuint64_t)(R.px * es), (cuuint64_t)(R.px * R.py * es)};
+        cuuint32_t box[3] = {(cuuint32_t)(T3X + 4), (cuuint32_t)(h->tune.t3y + 4), 1};
+        cuuint32_t estr[3] = {1, 1, 1};
+        for (int b = 0; b < 2; ++b)
+            for (int f = 0; f < 4; ++f) {
+                void *base = static_cast<char *>(h->buf[b][f]) + (size_t)R.off * es;
+                CUresult r = fn(&h->maps[((size_t)b * h->nruns + run) * 4 + f], dt, 3, base, dims,
+                                strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                if (r != CUDA_SUCCESS)
+                    return fail(h, ACM_ECUDA,
+                                "cuTensorMapEncodeTiled failed (" + std::to_string(r) + ")");
+            }
+    }
     h->maps_ok = true;
     return ACM_OK;
 }
@@ -243,8 +265,21 @@ acm_status create_common(const acm_params *params, int nruns, acm_handle **out)
         if (validate(params[r], why) != ACM_OK)
             return fail(nullptr, ACM_EINVAL, "run " + std::to_string(r) + ": " + why);
     const acm_params &p0 = params[0];
-    if (nruns > 1) {
-        if (p0.dim != 2) return fail(nullptr, ACM_EINVAL, "batches are 2D only");
+    if (p0.dim == 3 && (nruns > 1 || p0.bc[4] == ACM_BC_HALO)) {
+        // the runs are z-slabs of one grid
+        for (int r = 0; r < nruns; ++r) {
+            const acm_params &p = params[r];
+            if (p.dim != 3 || p.bc[4] != ACM_BC_HALO)
+                return fail(nullptr, ACM_EINVAL,
+                            "3D batches are sub-domains: every run needs ACM_BC_HALO z faces");
+            if (p.nx != p0.nx || p.ny != p0.ny || p.precision != p0.precision ||
+                p.dt != p0.dt || p.nu != p0.nu || p.rho0 != p0.rho0 ||
+                p.sat_mask != p0.sat_mask || p.g[0] != p0.g[0] || p.g[1] != p0.g[1] ||
+                p.g[2] != p0.g[2])
+                return fail(nullptr, ACM_EINVAL,
+                            "sub-domains must share nx, ny, precision and the physical parameters");
+        }
+    } else if (nruns > 1) {
         for (int r = 1; r < nruns; ++r) {
             const acm_params &p = params[r];
             if (p.dim != p0.dim || p.precision != p0.precision || p.two_phase != p0.two_phase)
@@ -280,8 +315,9 @@ acm_status create_common(const acm_params *params, int nruns, acm_handle **out)
     for (int r = 0; r < nruns; ++r) {
         RunDesc d = describe(params[r]);
         d.off = (long long)off;
-        const size_t n = (size_t)d.px * d.py * d.nz;
+        const size_t n = (size_t)d.px * d.py * (d.nz + 2 * d.zg);
         off += (n + 31) / 32 * 32;
+        if (d.zg) h->halo = true;
         h->runs.push_back(d);
         const long long np = (long long)d.nx * d.ny * d.nz;
         h->npoints.push_back(np);
@@ -359,9 +395,18 @@ template <typename T>
 cudaError_t one_step(acm_handle *h, int from)
 {
     Fields<T> in = fields_of<T>(h, from), out = fields_of<T>(h, 1 - from);
-    if (h->dim == 3)
-        return launch_step3d<T>(h->maps[from], out, h->runs[0], h->derr, h->tune.zchunks,
-                                h->tune.t3y, h->sms, h->stream);
+    if (h->dim == 3) {
+        cudaError_t e = cudaSuccess;
+        if (h->halo) {
+            const RunDesc &R = h->runs[0];
+            e = launch_halo<T>(h->druns, h->nruns, R.px * R.py, in, h->stream);
+        }
+        // one launch per sub-domain (a single launch for one periodic grid)
+        for (int r = 0; r < h->nruns && e == cudaSuccess; ++r)
+            e = launch_step3d<T>(&h->maps[((size_t)from * h->nruns + r) * 4], out, h->runs[r],
+                                 h->derr, h->tune.zchunks, h->tune.t3y, h->sms, h->stream);
+        return e;
+    }
     int blocks = h->tune.blocks;
     if (blocks <= 0) blocks = h->sms * step2d_max_blocks_per_sm<T>(h->two_phase);
     return launch_step2d<T>(h->druns, h->dwork, h->nwork, h->two_phase, in, out, h->derr, blocks,

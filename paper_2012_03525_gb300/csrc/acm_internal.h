@@ -44,6 +44,8 @@ struct RunDesc {
     long long off;      // element offset of the run inside each field pool
     long long px, py;   // storage pitch (elements) in x and y (3D: padded)
     int pad;            // ghost layers in x and y (3D TMA layout), 0 in 2D
+    int zg;             // ghost planes below (and above) the run: 2 for a 3D
+                        // sub-domain (ACM_BC_HALO z faces), else 0
     double rho0, dt, cs2, nu;
     double g[3], lid[3];
     double a, kappa, M; // two-phase coefficients
@@ -101,6 +103,13 @@ template <typename T>
 cudaError_t launch_reduce(const RunDesc *druns, int nruns, int dim, Fields<T> cur, const T *pu,
                           const T *pv, const T *pw, double *dpartials, int blocks_per_run,
                           double *dout, cudaStream_t s);
+
+// Halo exchange of 3D sub-domains (runs 0..nruns-1 form a ring along z):
+// copies the two boundary planes of every run into the ghost planes of its
+// neighbours, all four fields of f, one launch.
+template <typename T>
+cudaError_t launch_halo(const RunDesc *druns, int nruns, long long plane, Fields<T> f,
+                        cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_scan_nonfinite(const T *a, const T *b, long long n, unsigned *err,

@@ -22,7 +22,7 @@ __device__ __forceinline__ long long storage_index(const RunDesc &R, int dim, lo
     const long long rem = i - z * nxy;
     const long long y = rem / R.nx;
     const long long x = rem - y * R.nx;
-    return R.off + (z * R.py + y + R.pad) * R.px + x + R.pad;
+    return R.off + ((z + R.zg) * R.py + y + R.pad) * R.px + x + R.pad;
 }
 
 template <typename T>
@@ -118,7 +118,7 @@ __global__ void k_import(const double *__restrict__ src, T *__restrict__ dst, Ru
         long long x = rem % R.px - R.pad;
         y = ((y % R.ny) + R.ny) % R.ny;
         x = ((x % R.nx) + R.nx) % R.nx;
-        dst[R.off + i] = (T)(src[(z * R.ny + y) * R.nx + x] - shift);
+        dst[R.off + R.zg * R.px * R.py + i] = (T)(src[(z * R.ny + y) * R.nx + x] - shift);
     }
 }
 

@@ -25,7 +25,9 @@
 // Storage is padded by T3PAD ghost nodes in x and y (not in z).  Every output
 // node on the first/last two columns/rows is also written to its periodic
 // image in the ghost layers, so the next step's TMA boxes never wrap in x/y;
-// z wraps through the box coordinate.  Padding also keeps every box start on a
+// z wraps through the box coordinate, except in a sub-domain (one z-slab of
+// a larger grid), whose two ghost planes beyond each z face hold the
+// neighbouring slabs' planes.  Padding also keeps every box start on a
 // 16-byte boundary (x start = tile x0, a multiple of 32 elements).
 #include <algorithm>
 #include <type_traits>
@@ -121,115 +123,132 @@ struct Col {
     T r[2], u[2], v[2], w[2];
 };
 
-// Eq. (2.11) for one node from its 7-point neighbourhood (index order
-// C, E, W, N, S, U, D) of rho', u, v, w and Delta rho; returns the new state.
-// Written as chains of fused multiply-adds.
-template <typename T, bool GRAV>
-__device__ __forceinline__ void node_update(const T (&r)[7], const T (&u)[7], const T (&v)[7],
-                                            const T (&w)[7], const T (&d)[7], T rho0, T hdt,
-                                            T hdtcs2, T nudt, T hsatm, T dt, T gx, T gy, T gz,
-                                            T &rn, T &un, T &vn, T &wn)
-{
-    T mx[7], my[7], mz[7];
-#pragma unroll
-    for (int k = 0; k < 7; ++k) {
-        const T q = rho0 + r[k];
-        mx[k] = q * u[k];
-        my[k] = q * v[k];
-        mz[k] = q * w[k];
-    }
-    // twice the centred differences d_b(rho u_a u_b)
-    auto flux = [&](const T (&m)[7]) {
-        T f = m[1] * u[1];
-        f = fma(-m[2], u[2], f);
-        f = fma(m[3], v[3], f);
-        f = fma(-m[4], v[4], f);
-        f = fma(m[5], w[5], f);
-        return fma(-m[6], w[6], f);
-    };
-    auto lap = [&](const T (&m)[7]) {
-        return fma(T(-6), m[0], ((m[1] + m[2]) + (m[3] + m[4])) + (m[5] + m[6]));
-    };
-    const T rho1 = rho0 + r[0] + d[0];
-    const T inv = Prec<T>::recip(rho1);
-    T rx = nudt * lap(mx), ry = nudt * lap(my), rz = nudt * lap(mz);
-    rx = fma(-hdt, flux(mx), rx);
-    ry = fma(-hdt, flux(my), ry);
-    rz = fma(-hdt, flux(mz), rz);
-    rx = fma(-hdtcs2, r[1] - r[2], rx);
-    ry = fma(-hdtcs2, r[3] - r[4], ry);
-    rz = fma(-hdtcs2, r[5] - r[6], rz);
-    rx = fma(-hsatm, d[1] - d[2], rx);
-    ry = fma(-hsatm, d[3] - d[4], ry);
-    rz = fma(-hsatm, d[5] - d[6], rz);
-    if (GRAV) {
-        const T fb = dt * rho1;
-        rx = fma(fb, gx, rx);
-        ry = fma(fb, gy, ry);
-        rz = fma(fb, gz, rz);
-    }
-    un = fma(fma(-d[0], u[0], rx), inv, u[0]);
-    vn = fma(fma(-d[0], v[0], ry), inv, v[0]);
-    wn = fma(fma(-d[0], w[0], rz), inv, w[0]);
-    rn = r[0] + d[0];
-}
+// A thread's two nodes (a = lower row, b = upper row) travel as a pair
+// V2<T>: float2 for FP32 storage, whose arithmetic is issued as packed FP32
+// instructions (FFMA2/FADD2/FMUL2, sm_100 and later), double2 for FP64 (two
+// scalar operations).  Every operation is an explicit round-to-nearest
+// intrinsic, never contracted by the compiler, so a node's value does not
+// depend on where its arithmetic was inlined (z-chunk prologue or loop,
+// own node or a neighbour's ring) and a grid split into sub-domains gives
+// the same bits as the whole grid.
+template <typename T>
+struct V2T;
+template <>
+struct V2T<float> {
+    using type = float2;
+};
+template <>
+struct V2T<double> {
+    using type = double2;
+};
+template <typename T>
+using V2 = typename V2T<T>::type;
 
-// Packed FP32 (two lanes per instruction, sm_100+ FFMA2/FADD2/FMUL2) for the
-// FP32 instantiation: a thread's two nodes (lane x = lower node a, lane y =
-// upper node b) run through the same arithmetic, so every operation of
-// Eq. (2.10) and Eq. (2.11) on the own nodes is issued once for both.  Each
-// lane rounds exactly like the scalar operation it replaces.
-__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
-__device__ __forceinline__ float2 splat(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
+template <typename T>
+__device__ __forceinline__ V2<T> splat(T a)
+{
+    return mk(a, a);
+}
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ double2 add2(double2 a, double2 b)
+{
+    return make_double2(__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y));
+}
+__device__ __forceinline__ double2 mul2(double2 a, double2 b)
+{
+    return make_double2(__dmul_rn(a.x, b.x), __dmul_rn(a.y, b.y));
+}
+__device__ __forceinline__ double2 fma2(double2 a, double2 b, double2 c)
+{
+    return make_double2(__fma_rn(a.x, b.x, c.x), __fma_rn(a.y, b.y, c.y));
+}
+// scalar counterparts (ring points of the Delta-rho window)
+__device__ __forceinline__ float add1(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float mul1(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fma1(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double add1(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double mul1(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double fma1(double a, double b, double c) { return __fma_rn(a, b, c); }
 
-// reciprocal of rho^{n+1} = 1 + O(Ma^2): the hardware approximation (1 ulp)
-// suffices, since it only scales the O(Ma^2)-relative increment of u
-__device__ __forceinline__ float rcp_approx(float x)
+// 1 / rho^{n+1}.  FP32: the hardware approximation (1 ulp) suffices, since
+// it only scales the increment of u, which is O(Ma^2) relative to u.
+__device__ __forceinline__ float recip(float x)
 {
     float y;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
+__device__ __forceinline__ double recip(double x) { return __drcp_rn(x); }
 
-// coefficient pairs of the packed update (negated where a term is subtracted)
+// coefficient pairs (negated copies where a term is subtracted, so that no
+// operand needs negating)
+template <typename T>
 struct K2 {
-    float2 rho0, hdt, nhdt, hdtcs2, nhdtcs2, nudt, hsatm, nhsatm, m6, satc, dt, gx, gy, gz;
+    V2<T> rho0, hdt, nhdt, hdtcs2, nhdtcs2, nudt, hsatm, nhsatm, m6, satc, dt, gx, gy, gz;
 };
 
-// Eq. (2.11) for both own nodes; arrays in the order C, E, W, N, S, U, D.
-// Differences are split into a positive and a negative chain so that no
-// operand needs negating: -hdt (P - N) = fma(-hdt, P, hdt N).
-template <bool GRAV>
-__device__ __forceinline__ void node_update2(const float2 (&r)[7], const float2 (&u)[7],
-                                             const float2 (&v)[7], const float2 (&w)[7],
-                                             const float2 (&d)[7], const K2 &K, float2 &rn,
-                                             float2 &un, float2 &vn, float2 &wn)
+// Eq. (2.10): Delta rho from a node's 7-point neighbourhood (E, W, N, S, U,
+// D), the same operation order for a pair and for a single ring node:
+//   Delta rho = (1/2 cs^2 dt^2) Lap(rho) - (dt/2) [(m_E + m_N + m_U) - (m_W + m_S + m_D)]
+// with m = (rho0 + rho') u_b along each axis b.
+template <typename T>
+__device__ __forceinline__ V2<T> delta2(const K2<T> &K, V2<T> rC, V2<T> rE, V2<T> rW, V2<T> rN,
+                                        V2<T> rS, V2<T> rU, V2<T> rD, V2<T> uE, V2<T> uW,
+                                        V2<T> vN, V2<T> vS, V2<T> wU, V2<T> wD)
 {
-    float2 mx[7], my[7], mz[7];
+    const V2<T> P = fma2(add2(K.rho0, rE), uE, fma2(add2(K.rho0, rN), vN, mul2(add2(K.rho0, rU), wU)));
+    const V2<T> N = fma2(add2(K.rho0, rW), uW, fma2(add2(K.rho0, rS), vS, mul2(add2(K.rho0, rD), wD)));
+    const V2<T> lap = fma2(K.m6, rC, add2(add2(add2(rE, rW), add2(rN, rS)), add2(rU, rD)));
+    return fma2(K.satc, lap, fma2(K.nhdt, P, mul2(K.hdt, N)));
+}
+template <typename T>
+__device__ __forceinline__ T delta1(const K2<T> &K, T rC, T rE, T rW, T rN, T rS, T rU, T rD,
+                                    T uE, T uW, T vN, T vS, T wU, T wD)
+{
+    const T r0 = K.rho0.x;
+    const T P = fma1(add1(r0, rE), uE, fma1(add1(r0, rN), vN, mul1(add1(r0, rU), wU)));
+    const T N = fma1(add1(r0, rW), uW, fma1(add1(r0, rS), vS, mul1(add1(r0, rD), wD)));
+    const T lap = fma1(K.m6.x, rC, add1(add1(add1(rE, rW), add1(rN, rS)), add1(rU, rD)));
+    return fma1(K.satc.x, lap, fma1(K.nhdt.x, P, mul1(K.hdt.x, N)));
+}
+
+// Eq. (2.11) for a node pair; arrays in the order C, E, W, N, S, U, D of
+// rho', u, v, w and Delta rho.  Differences are split into a positive and a
+// negative chain: -hdt (P - N) = fma(-hdt, P, hdt N).  Then
+// u^{n+1} = u + (RHS - Delta rho u) / rho^{n+1}.
+template <typename T, bool GRAV>
+__device__ __forceinline__ void node_update2(const V2<T> (&r)[7], const V2<T> (&u)[7],
+                                             const V2<T> (&v)[7], const V2<T> (&w)[7],
+                                             const V2<T> (&d)[7], const K2<T> &K, V2<T> &rn,
+                                             V2<T> &un, V2<T> &vn, V2<T> &wn)
+{
+    using P2 = V2<T>;
+    P2 mx[7], my[7], mz[7];
 #pragma unroll
     for (int k = 0; k < 7; ++k) {
-        const float2 q = add2(K.rho0, r[k]);
+        const P2 q = add2(K.rho0, r[k]);
         mx[k] = mul2(q, u[k]);
         my[k] = mul2(q, v[k]);
         mz[k] = mul2(q, w[k]);
     }
-    auto lap = [&](const float2 (&m)[7]) {
+    auto lap = [&](const P2 (&m)[7]) {
         return fma2(K.m6, m[0], add2(add2(add2(m[1], m[2]), add2(m[3], m[4])), add2(m[5], m[6])));
     };
-    // R += -hdt * (twice the centred difference of m u_b over b)
-    auto flux = [&](const float2 (&m)[7], float2 R) {
-        const float2 P = fma2(m[1], u[1], fma2(m[3], v[3], mul2(m[5], w[5])));
-        const float2 N = fma2(m[2], u[2], fma2(m[4], v[4], mul2(m[6], w[6])));
+    // R - (dt/2) [twice-centred d_b (m u_b)]
+    auto flux = [&](const P2 (&m)[7], P2 R) {
+        const P2 P = fma2(m[1], u[1], fma2(m[3], v[3], mul2(m[5], w[5])));
+        const P2 N = fma2(m[2], u[2], fma2(m[4], v[4], mul2(m[6], w[6])));
         return fma2(K.nhdt, P, fma2(K.hdt, N, R));
     };
-    const float2 rho1 = add2(add2(K.rho0, r[0]), d[0]);
-    const float2 inv = f2(rcp_approx(rho1.x), rcp_approx(rho1.y));
-    float2 rx = flux(mx, mul2(K.nudt, lap(mx)));
-    float2 ry = flux(my, mul2(K.nudt, lap(my)));
-    float2 rz = flux(mz, mul2(K.nudt, lap(mz)));
+    const P2 rho1 = add2(add2(K.rho0, r[0]), d[0]);
+    const P2 inv = mk(recip(rho1.x), recip(rho1.y));
+    P2 rx = flux(mx, mul2(K.nudt, lap(mx)));
+    P2 ry = flux(my, mul2(K.nudt, lap(my)));
+    P2 rz = flux(mz, mul2(K.nudt, lap(mz)));
     rx = fma2(K.nhdtcs2, r[1], fma2(K.hdtcs2, r[2], rx));
     ry = fma2(K.nhdtcs2, r[3], fma2(K.hdtcs2, r[4], ry));
     rz = fma2(K.nhdtcs2, r[5], fma2(K.hdtcs2, r[6], rz));
@@ -237,12 +256,12 @@ __device__ __forceinline__ void node_update2(const float2 (&r)[7], const float2 
     ry = fma2(K.nhsatm, d[3], fma2(K.hsatm, d[4], ry));
     rz = fma2(K.nhsatm, d[5], fma2(K.hsatm, d[6], rz));
     if (GRAV) {
-        const float2 fb = mul2(K.dt, rho1);
+        const P2 fb = mul2(K.dt, rho1);
         rx = fma2(fb, K.gx, rx);
         ry = fma2(fb, K.gy, ry);
         rz = fma2(fb, K.gz, rz);
     }
-    const float2 nd = f2(-d[0].x, -d[0].y);
+    const P2 nd = mk(-d[0].x, -d[0].y);
     un = fma2(fma2(nd, u[0], rx), inv, u[0]);
     vn = fma2(fma2(nd, v[0], ry), inv, v[0]);
     wn = fma2(fma2(nd, w[0], rz), inv, w[0]);
@@ -325,12 +344,10 @@ __global__ void __launch_bounds__(T3X *TY / 2, Prec<T>::MINB * 16 / TY)
     const T satc = C[C_SATC], hsatm = T(0.5) * C[C_SATM];
     const T gfx = C[C_GX], gfy = C[C_GY], gfz = C[C_GZ];
     constexpr uint32_t TX_BYTES = 4u * G::PLANE * sizeof(T);
-    constexpr bool PACK = std::is_same<T, float>::value;
-    const K2 K{splat((float)rho0),  splat((float)hdt),    splat(-(float)hdt),
-               splat((float)hdtcs2), splat(-(float)hdtcs2), splat((float)nudt),
-               splat((float)hsatm), splat(-(float)hsatm), splat(-6.0f),
-               splat((float)satc),  splat((float)dt),     splat((float)gfx),
-               splat((float)gfy),   splat((float)gfz)};
+    using P2 = V2<T>;
+    const K2<T> K{splat(rho0), splat(hdt),   splat(-hdt),   splat(hdtcs2), splat(-hdtcs2),
+                  splat(nudt), splat(hsatm), splat(-hsatm), splat(T(-6)),  splat(satc),
+                  splat(dt),   splat(gfx),   splat(gfy),    splat(gfz)};
 
     if (tid == 0) {
         for (int s = 0; s < NSLOT; ++s) mbar_init(&bar[s], 1);
@@ -362,8 +379,12 @@ __global__ void __launch_bounds__(T3X *TY / 2, Prec<T>::MINB * 16 / TY)
     // of the next completion of slot s's barrier.
     uint32_t phase = 0;
     auto issue = [&](int s, int p, int x0, int y0) {
-        int zw = p % nz;
-        if (zw < 0) zw += nz;
+        // periodic grids wrap z; a sub-domain reads its ghost planes
+        int zw = p + R.zg;
+        if (R.zg == 0) {
+            zw = p % nz;
+            if (zw < 0) zw += nz;
+        }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_expect_tx(&bar[s], TX_BYTES);
         T *dst = S + s * 4 * PE;
@@ -396,41 +417,17 @@ __global__ void __launch_bounds__(T3X *TY / 2, Prec<T>::MINB * 16 / TY)
     auto delta_rho = [&](int sm, int s0, int sp, T *dw, const Col<T> &Cd, const Col<T> &C0,
                          const Col<T> &Cu, T (&dout)[2]) {
         const T *pr = S + s0 * 4 * PE, *pu = pr + PE, *pv = pr + 2 * PE;
-        if constexpr (PACK) {
-            // both own nodes at once (lane x: node a, whose N is node b;
+        {   // both own nodes at once (lane x: node a, whose N is node b;
             // lane y: node b, whose S is node a)
-            const float2 rE = f2(pr[ca + 1], pr[cb + 1]), rW = f2(pr[ca - 1], pr[cb - 1]);
-            const float2 rN = f2(C0.r[1], pr[cb + RW]), rS = f2(pr[ca - RW], C0.r[0]);
-            const float2 uE = f2(pu[ca + 1], pu[cb + 1]), uW = f2(pu[ca - 1], pu[cb - 1]);
-            const float2 vN = f2(C0.v[1], pv[cb + RW]), vS = f2(pv[ca - RW], C0.v[0]);
-            const float2 rU = f2(Cu.r[0], Cu.r[1]), wU = f2(Cu.w[0], Cu.w[1]);
-            const float2 rD = f2(Cd.r[0], Cd.r[1]), wD = f2(Cd.w[0], Cd.w[1]);
-            const float2 P = fma2(add2(K.rho0, rE), uE,
-                                  fma2(add2(K.rho0, rN), vN, mul2(add2(K.rho0, rU), wU)));
-            const float2 N = fma2(add2(K.rho0, rW), uW,
-                                  fma2(add2(K.rho0, rS), vS, mul2(add2(K.rho0, rD), wD)));
-            const float2 lap = fma2(K.m6, f2(C0.r[0], C0.r[1]),
-                                    add2(add2(add2(rE, rW), add2(rN, rS)), add2(rU, rD)));
-            const float2 dd = fma2(K.satc, lap, fma2(K.nhdt, P, mul2(K.hdt, N)));
+            const P2 dd = delta2<T>(K, mk(C0.r[0], C0.r[1]), mk(pr[ca + 1], pr[cb + 1]),
+                                    mk(pr[ca - 1], pr[cb - 1]), mk(C0.r[1], pr[cb + RW]),
+                                    mk(pr[ca - RW], C0.r[0]), mk(Cu.r[0], Cu.r[1]),
+                                    mk(Cd.r[0], Cd.r[1]), mk(pu[ca + 1], pu[cb + 1]),
+                                    mk(pu[ca - 1], pu[cb - 1]), mk(C0.v[1], pv[cb + RW]),
+                                    mk(pv[ca - RW], C0.v[0]), mk(Cu.w[0], Cu.w[1]),
+                                    mk(Cd.w[0], Cd.w[1]));
             dout[0] = dd.x;
             dout[1] = dd.y;
-        } else {
-        {   // lower node a: N is node b
-            const T rE = pr[ca + 1], rW = pr[ca - 1], rS = pr[ca - RW], rN = C0.r[1];
-            const T div = ((rho0 + rE) * pu[ca + 1] - (rho0 + rW) * pu[ca - 1]) +
-                          ((rho0 + rN) * C0.v[1] - (rho0 + rS) * pv[ca - RW]) +
-                          ((rho0 + Cu.r[0]) * Cu.w[0] - (rho0 + Cd.r[0]) * Cd.w[0]);
-            const T lap = (rE + rW) + (rN + rS) + (Cu.r[0] + Cd.r[0]) - T(6) * C0.r[0];
-            dout[0] = satc * lap - hdt * div;
-        }
-        {   // upper node b: S is node a
-            const T rE = pr[cb + 1], rW = pr[cb - 1], rN = pr[cb + RW], rS = C0.r[0];
-            const T div = ((rho0 + rE) * pu[cb + 1] - (rho0 + rW) * pu[cb - 1]) +
-                          ((rho0 + rN) * pv[cb + RW] - (rho0 + rS) * C0.v[0]) +
-                          ((rho0 + Cu.r[1]) * Cu.w[1] - (rho0 + Cd.r[1]) * Cd.w[1]);
-            const T lap = (rE + rW) + (rN + rS) + (Cu.r[1] + Cd.r[1]) - T(6) * C0.r[1];
-            dout[1] = satc * lap - hdt * div;
-        }
         }
         dw[da] = dout[0];
         dw[db] = dout[1];
@@ -438,12 +435,9 @@ __global__ void __launch_bounds__(T3X *TY / 2, Prec<T>::MINB * 16 / TY)
             const int c = ring_c;
             const T *rd = S + sm * 4 * PE, *wd = rd + 3 * PE;
             const T *ru = S + sp * 4 * PE, *wu = ru + 3 * PE;
-            const T div = ((rho0 + pr[c + 1]) * pu[c + 1] - (rho0 + pr[c - 1]) * pu[c - 1]) +
-                          ((rho0 + pr[c + RW]) * pv[c + RW] - (rho0 + pr[c - RW]) * pv[c - RW]) +
-                          ((rho0 + ru[c]) * wu[c] - (rho0 + rd[c]) * wd[c]);
-            const T lap = (pr[c + 1] + pr[c - 1]) + (pr[c + RW] + pr[c - RW]) + (ru[c] + rd[c]) -
-                          T(6) * pr[c];
-            dw[ring_d] = satc * lap - hdt * div;
+            dw[ring_d] = delta1<T>(K, pr[c], pr[c + 1], pr[c - 1], pr[c + RW], pr[c - RW], ru[c],
+                                   rd[c], pu[c + 1], pu[c - 1], pv[c + RW], pv[c - RW], wu[c],
+                                   wd[c]);
         }
     };
 
@@ -480,7 +474,8 @@ __global__ void __launch_bounds__(T3X *TY / 2, Prec<T>::MINB * 16 / TY)
                                 y0 + TY <= ny - T3PAD;
         const bool own_a = gx < nx && gya < ny, own_b = gx < nx && gyb < ny;
         const bool edge = gx < T3PAD || gx >= nx - T3PAD || gya < T3PAD || gyb >= ny - T3PAD;
-        const long long base_a = R.off + (long long)(gya + T3PAD) * PX + (gx + T3PAD);
+        const long long base_a =
+            R.off + R.zg * PXY + (long long)(gya + T3PAD) * PX + (gx + T3PAD);
         auto store2 = [&](long long ga, T ra, T ua, T va, T wa, T rb, T ub, T vb, T wb) {
             if (plain_tile) {
                 out.f[F_R][ga] = ra;
@@ -531,53 +526,29 @@ __global__ void __launch_bounds__(T3X *TY / 2, Prec<T>::MINB * 16 / TY)
             const T *pr = S + S0 * 4 * PE, *pu = pr + PE, *pv = pr + 2 * PE, *pw = pr + 3 * PE;
             const T *dz = SD + (z & 1) * P1;
             const Col<T> &Xm = Q[SM], &X0 = Q[S0], &Xp = Q[S1];
-            T ra, ua, va, wa, rb, ub, vb, wb;
-            if constexpr (PACK) {
-                const float2 r[7] = {f2(X0.r[0], X0.r[1]), f2(pr[ca + 1], pr[cb + 1]),
-                                     f2(pr[ca - 1], pr[cb - 1]), f2(X0.r[1], pr[cb + RW]),
-                                     f2(pr[ca - RW], X0.r[0]), f2(Xp.r[0], Xp.r[1]),
-                                     f2(Xm.r[0], Xm.r[1])};
-                const float2 u[7] = {f2(X0.u[0], X0.u[1]), f2(pu[ca + 1], pu[cb + 1]),
-                                     f2(pu[ca - 1], pu[cb - 1]), f2(X0.u[1], pu[cb + RW]),
-                                     f2(pu[ca - RW], X0.u[0]), f2(Xp.u[0], Xp.u[1]),
-                                     f2(Xm.u[0], Xm.u[1])};
-                const float2 v[7] = {f2(X0.v[0], X0.v[1]), f2(pv[ca + 1], pv[cb + 1]),
-                                     f2(pv[ca - 1], pv[cb - 1]), f2(X0.v[1], pv[cb + RW]),
-                                     f2(pv[ca - RW], X0.v[0]), f2(Xp.v[0], Xp.v[1]),
-                                     f2(Xm.v[0], Xm.v[1])};
-                const float2 w[7] = {f2(X0.w[0], X0.w[1]), f2(pw[ca + 1], pw[cb + 1]),
-                                     f2(pw[ca - 1], pw[cb - 1]), f2(X0.w[1], pw[cb + RW]),
-                                     f2(pw[ca - RW], X0.w[0]), f2(Xp.w[0], Xp.w[1]),
-                                     f2(Xm.w[0], Xm.w[1])};
-                const float2 d[7] = {f2(D[S0][0], D[S0][1]), f2(dz[da + 1], dz[db + 1]),
-                                     f2(dz[da - 1], dz[db - 1]), f2(D[S0][1], dz[db + RW1]),
-                                     f2(dz[da - RW1], D[S0][0]), f2(D[S1][0], D[S1][1]),
-                                     f2(D[SM][0], D[SM][1])};
-                float2 rn, un, vn, wn;
-                node_update2<GRAV>(r, u, v, w, d, K, rn, un, vn, wn);
-                ra = rn.x; ua = un.x; va = vn.x; wa = wn.x;
-                rb = rn.y; ub = un.y; vb = vn.y; wb = wn.y;
-            } else {
-            {   // lower node a: N neighbour is node b
-                const T r[7] = {X0.r[0], pr[ca + 1], pr[ca - 1], X0.r[1], pr[ca - RW], Xp.r[0], Xm.r[0]};
-                const T u[7] = {X0.u[0], pu[ca + 1], pu[ca - 1], X0.u[1], pu[ca - RW], Xp.u[0], Xm.u[0]};
-                const T v[7] = {X0.v[0], pv[ca + 1], pv[ca - 1], X0.v[1], pv[ca - RW], Xp.v[0], Xm.v[0]};
-                const T w[7] = {X0.w[0], pw[ca + 1], pw[ca - 1], X0.w[1], pw[ca - RW], Xp.w[0], Xm.w[0]};
-                const T d[7] = {D[S0][0], dz[da + 1], dz[da - 1], D[S0][1], dz[da - RW1], D[S1][0], D[SM][0]};
-                node_update<T, GRAV>(r, u, v, w, d, rho0, hdt, hdtcs2, nudt, hsatm, dt, gfx, gfy,
-                                     gfz, ra, ua, va, wa);
-            }
-            {   // upper node b: S neighbour is node a
-                const T r[7] = {X0.r[1], pr[cb + 1], pr[cb - 1], pr[cb + RW], X0.r[0], Xp.r[1], Xm.r[1]};
-                const T u[7] = {X0.u[1], pu[cb + 1], pu[cb - 1], pu[cb + RW], X0.u[0], Xp.u[1], Xm.u[1]};
-                const T v[7] = {X0.v[1], pv[cb + 1], pv[cb - 1], pv[cb + RW], X0.v[0], Xp.v[1], Xm.v[1]};
-                const T w[7] = {X0.w[1], pw[cb + 1], pw[cb - 1], pw[cb + RW], X0.w[0], Xp.w[1], Xm.w[1]};
-                const T d[7] = {D[S0][1], dz[db + 1], dz[db - 1], dz[db + RW1], D[S0][0], D[S1][1], D[SM][1]};
-                node_update<T, GRAV>(r, u, v, w, d, rho0, hdt, hdtcs2, nudt, hsatm, dt, gfx, gfy,
-                                     gfz, rb, ub, vb, wb);
-            }
-            }
-            store2(base_a + (long long)z * PXY, ra, ua, va, wa, rb, ub, vb, wb);
+            const P2 r[7] = {mk(X0.r[0], X0.r[1]), mk(pr[ca + 1], pr[cb + 1]),
+                             mk(pr[ca - 1], pr[cb - 1]), mk(X0.r[1], pr[cb + RW]),
+                             mk(pr[ca - RW], X0.r[0]), mk(Xp.r[0], Xp.r[1]),
+                             mk(Xm.r[0], Xm.r[1])};
+            const P2 u[7] = {mk(X0.u[0], X0.u[1]), mk(pu[ca + 1], pu[cb + 1]),
+                             mk(pu[ca - 1], pu[cb - 1]), mk(X0.u[1], pu[cb + RW]),
+                             mk(pu[ca - RW], X0.u[0]), mk(Xp.u[0], Xp.u[1]),
+                             mk(Xm.u[0], Xm.u[1])};
+            const P2 v[7] = {mk(X0.v[0], X0.v[1]), mk(pv[ca + 1], pv[cb + 1]),
+                             mk(pv[ca - 1], pv[cb - 1]), mk(X0.v[1], pv[cb + RW]),
+                             mk(pv[ca - RW], X0.v[0]), mk(Xp.v[0], Xp.v[1]),
+                             mk(Xm.v[0], Xm.v[1])};
+            const P2 w[7] = {mk(X0.w[0], X0.w[1]), mk(pw[ca + 1], pw[cb + 1]),
+                             mk(pw[ca - 1], pw[cb - 1]), mk(X0.w[1], pw[cb + RW]),
+                             mk(pw[ca - RW], X0.w[0]), mk(Xp.w[0], Xp.w[1]),
+                             mk(Xm.w[0], Xm.w[1])};
+            const P2 d[7] = {mk(D[S0][0], D[S0][1]), mk(dz[da + 1], dz[db + 1]),
+                             mk(dz[da - 1], dz[db - 1]), mk(D[S0][1], dz[db + RW1]),
+                             mk(dz[da - RW1], D[S0][0]), mk(D[S1][0], D[S1][1]),
+                             mk(D[SM][0], D[SM][1])};
+            P2 rn, un, vn, wn;
+            node_update2<T, GRAV>(r, u, v, w, d, K, rn, un, vn, wn);
+            store2(base_a + (long long)z * PXY, rn.x, un.x, vn.x, wn.x, rn.y, un.y, vn.y, wn.y);
             return true;
         };
 

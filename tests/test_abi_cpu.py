@@ -56,6 +56,10 @@ def test_params_struct_layout_matches_header():
     (dict(shape=(8, 8), two_phase=True, theta_deg=float("nan")), "contact angle"),
     (dict(shape=(8, 8), sat_mask=4), "sat_mask"),
     (dict(shape=(8, 8), precision=7), "precision"),
+    (dict(shape=(8, 8), bc=[0, 0, 3, 3, 0, 0]), "z faces of 3D"),
+    (dict(shape=(4, 8, 8), bc=[0, 0, 0, 0, 3, 0]), "both faces"),
+    (dict(shape=(1, 8, 8), bc=[0, 0, 0, 0, 3, 3]), "nz >= 2"),
+    (dict(shape=(4, 8, 8), bc=[3, 3, 0, 0, 0, 0]), "z faces of 3D"),
 ])
 def test_invalid_params_rejected_on_host(lib, kw, msg):
     shape = kw.pop("shape")
@@ -81,3 +85,26 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.acm_sync(None) == acm.EINVAL
     assert lib.acm_destroy(None) == acm.OK
     assert lib.acm_nruns(None) == 0
+
+
+def test_3d_batches_must_be_matching_subdomains(lib):
+    # 3D runs without halo faces cannot be batched
+    a = acm.make_params((8, 8, 8))
+    arr = (acm.Params * 2)(a, a)
+    h = ctypes.c_void_p()
+    assert lib.acm_batch_create(arr, 2, ctypes.byref(h)) == acm.EINVAL
+    assert "sub-domains" in lib.acm_last_error(None).decode()
+    # slabs of different x-y size cannot form one grid
+    p = acm.subdomain_params((8, 8, 8), (4, 4))
+    p[1].nx = 16
+    arr = (acm.Params * 2)(*p)
+    assert lib.acm_batch_create(arr, 2, ctypes.byref(h)) == acm.EINVAL
+    assert "share" in lib.acm_last_error(None).decode()
+
+
+def test_subdomain_params_split():
+    p = acm.subdomain_params((10, 6, 8), (3, 7), nu=0.1)
+    assert [q.nz for q in p] == [3, 7]
+    assert all(q.bc[4] == q.bc[5] == acm.BC_HALO for q in p)
+    with pytest.raises(ValueError):
+        acm.subdomain_params((10, 6, 8), (3, 6))
