@@ -370,6 +370,71 @@ def run_closure(args):
     return 0
 
 
+def run_subdomains(args):
+    """The bench workload (3D TGV 256^3, FP32) split along z into S slabs
+    (S = 1, 2, 4, 8: sub-domains with ghost planes and a halo-copy kernel
+    before every step, the slab decomposition of a multi-GPU run emulated on
+    one GPU) against the same grid as one periodic handle: GLUPS of each, the
+    exchange's share of the step, and bitwise agreement of the fields."""
+    import numpy as np
+    import torch
+    from paper_2012_03525_gb300 import acm, build
+    from paper_2012_03525_gb300 import workloads as wl
+    build.build()
+    n = args.n
+    nu = wl.tgv3d_nu(n, U0, RE)
+    state = wl.tgv3d(n, U0)
+    stream = torch.cuda.Stream()
+    results, ref_fields = {}, None
+    for S in (1, 2, 4, 8):
+        parts = [n // S] * S
+        if S == 1:
+            solver = acm.Solver(acm.make_params((n, n, n), nu=nu, precision=acm.FP32_DEV))
+        else:
+            solver = acm.Solver(acm.subdomain_params((n, n, n), parts, nu=nu,
+                                                     precision=acm.FP32_DEV))
+        solver.set_stream(stream.cuda_stream)
+        z0 = 0
+        for r, k in enumerate(parts):
+            solver.set_fields(*[f[z0:z0 + k] for f in state], run=r)
+            z0 += k
+        solver.step(max(args.warmup, 64))
+        solver.sync()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        solver.step(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        solver.sync()
+        fields = [np.concatenate(p, axis=0) for p in
+                  zip(*[solver.fields(run=r)[:4] for r in range(len(parts))])]
+        solver.close()
+        if ref_fields is None:
+            ref_fields = fields
+        results[f"slabs_{S}"] = {
+            "GLUPS": n ** 3 * args.steps / (ms / 1e3) / 1e9, "ms_per_step": ms / args.steps,
+            "launches_per_step": S + (1 if S > 1 else 0),
+            "halo_bytes_per_step": 0 if S == 1 else S * 2 * 4 * 2 * (n + 4) * (n + 8) * 4,
+            "bitwise_equal_to_unsplit": all(np.array_equal(a, b)
+                                            for a, b in zip(fields, ref_fields))}
+    base = results["slabs_1"]["ms_per_step"]
+    for k, v in results.items():
+        v["overhead_vs_unsplit"] = v["ms_per_step"] / base - 1.0
+    print(json.dumps({
+        "metric": "GLUPS", "value": results["slabs_4"]["GLUPS"], "unit": "GLUPS", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": results["slabs_4"]["ms_per_step"], "higher_is_better": True,
+        "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"3D periodic TGV {n}^3 split into z-slabs (sub-domains with "
+                               "ghost planes, halo-copy kernel per step), FP32; value = 4 slabs",
+                   "slabs": [1, 2, 4, 8]},
+        "runs": results,
+    }))
+    return 0
+
+
 def run_dpsl(args):
     """The paper's doubly periodic shear layer (Section 3.3: N_L = 320,
     N_t = 16000, Re = 1e4, 0 <= t <= 1) timed end to end on the GPU in FP64
@@ -418,7 +483,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="tgv3d", choices=["tgv3d", "drops", "closure", "dpsl"],
+    ap.add_argument("--workload", default="tgv3d", choices=["tgv3d", "drops", "closure", "dpsl", "subdomains"],
                     help="tgv3d: the bench line; drops: the batched two-phase workload; "
                          "closure: the learned closure's time-to-eps comparison")
     ap.add_argument("--train-trajectories", type=int, default=32)
@@ -442,6 +507,8 @@ def main():
         return run_closure(args)
     if args.workload == "dpsl":
         return run_dpsl(args)
+    if args.workload == "subdomains":
+        return run_subdomains(args)
 
     import numpy as np
     import torch

@@ -39,6 +39,10 @@ struct acm_handle {
     std::vector<CUtensorMap> maps;  // 3D: [buffer][run][field]
     bool maps_ok = false;
     bool halo = false;              // 3D sub-domains (ACM_BC_HALO z faces)
+    // sub-domains step concurrently: slab r > 0 runs on side[r - 1], forked
+    // from and joined back into `stream` with events
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> ev;    // [0] fork, [r] join of slab r
     cudaGraphExec_t gexec = nullptr;
     Tuning tune;
     std::string err;
@@ -247,6 +251,8 @@ void release(acm_handle *h)
     if (h->dout) cudaFree(h->dout);
     if (h->dstage) cudaFree(h->dstage);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    for (cudaStream_t st : h->side) cudaStreamDestroy(st);
+    for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
 }
 
 bool field_used(const acm_handle *h, int f)
@@ -348,6 +354,12 @@ acm_status create_common(const acm_params *params, int nruns, acm_handle **out)
 
     CKB(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
     h->own_stream = true;
+    if (h->halo && nruns > 1) {
+        h->side.assign(nruns - 1, nullptr);
+        h->ev.assign(nruns, nullptr);
+        for (auto &st : h->side) CKB(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        for (auto &e : h->ev) CKB(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
     for (int b = 0; b < 2; ++b)
         for (int f = 0; f < NFIELD; ++f)
             if (field_used(h, f)) {
@@ -401,10 +413,22 @@ cudaError_t one_step(acm_handle *h, int from)
             const RunDesc &R = h->runs[0];
             e = launch_halo<T>(h->druns, h->nruns, R.px * R.py, in, h->stream);
         }
-        // one launch per sub-domain (a single launch for one periodic grid)
-        for (int r = 0; r < h->nruns && e == cudaSuccess; ++r)
-            e = launch_step3d<T>(&h->maps[((size_t)from * h->nruns + r) * 4], out, h->runs[r],
-                                 h->derr, h->tune.zchunks, h->tune.t3y, h->sms, h->stream);
+        // one launch per sub-domain (a single launch for one periodic grid);
+        // the slabs write disjoint planes, so their launches run concurrently
+        // on forked streams and the next step waits for all of them
+        const bool fork = !h->side.empty();
+        if (fork && e == cudaSuccess) e = cudaEventRecord(h->ev[0], h->stream);
+        for (int r = 0; r < h->nruns && e == cudaSuccess; ++r) {
+            cudaStream_t st = r == 0 ? h->stream : h->side[r - 1];
+            if (r > 0) e = cudaStreamWaitEvent(st, h->ev[0], 0);
+            if (e == cudaSuccess)
+                e = launch_step3d<T>(&h->maps[((size_t)from * h->nruns + r) * 4], out,
+                                     h->runs[r], h->derr, h->tune.zchunks, h->tune.t3y, h->sms,
+                                     st);
+            if (r > 0 && e == cudaSuccess) e = cudaEventRecord(h->ev[r], st);
+        }
+        for (int r = 1; r < h->nruns && fork && e == cudaSuccess; ++r)
+            e = cudaStreamWaitEvent(h->stream, h->ev[r], 0);
         return e;
     }
     int blocks = h->tune.blocks;
