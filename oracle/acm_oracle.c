@@ -33,6 +33,10 @@
  *     F_ST = -phi^n grad mu^n enters the momentum update (Section 2, the
  *     two-phase paragraph), mu = 4 a phi (phi^2-1) - kappa Lap(phi),
  *     a = 3 sigma/(4W), kappa = 3 sigma W/8.
+ *   - the MAMEs predictor-corrector (Eqs. 2.6-2.9, oracle_step_mames), kept
+ *     as the comparison scheme: centred first differences, compact second
+ *     differences for d_aa, the centred four-point mixed difference for
+ *     d_ab (a != b), periodic grids only.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -409,6 +413,120 @@ int oracle_step(const oracle_params *p, double *rho, double *u, double *v,
     for (int d = 0; d < 3; ++d) { free(m[d]); free(mnew[d]); }
     free(mu); free(mus); free(phis); free(R);
     return 0;
+}
+
+/* ---- MAMEs predictor-corrector (Section 2, Eqs. 2.6-2.9): the scheme the
+   simplified one-step update replaces, kept as a comparison scheme ----
+
+   Spatial operators (the paper does not print them for this scheme; these
+   are the second-order centred forms on the same grid):
+     D_a f      centred first difference (Eq. 2.12),
+     D_aa f     compact second difference f(+a) - 2 f + f(-a),
+     D_ab f     (a != b) centred mixed difference
+                (f(+a+b) - f(+a-b) - f(-a+b) + f(-a-b)) / 4,
+     L f        sum_a D_aa f (Eq. 2.13).
+   Pi_ab = rho u_a u_b + p delta_ab with p = c_s^2 rho.  Periodic grids only. */
+static double dmix(const grid_t *G, const double *f, int i, int j, int k, int a, int b)
+{
+    int ea[3] = {0, 0, 0}, eb[3] = {0, 0, 0};
+    ea[a] = 1;
+    eb[b] = 1;
+    if (a == b)
+        return f[gidx(G, i + ea[0], j + ea[1], k + ea[2])] - 2.0 * f[gidx(G, i, j, k)] +
+               f[gidx(G, i - ea[0], j - ea[1], k - ea[2])];
+    double pp = f[gidx(G, i + ea[0] + eb[0], j + ea[1] + eb[1], k + ea[2] + eb[2])];
+    double pm = f[gidx(G, i + ea[0] - eb[0], j + ea[1] - eb[1], k + ea[2] - eb[2])];
+    double mp = f[gidx(G, i - ea[0] + eb[0], j - ea[1] + eb[1], k - ea[2] + eb[2])];
+    double mm = f[gidx(G, i - ea[0] - eb[0], j - ea[1] - eb[1], k - ea[2] - eb[2])];
+    return (pp - pm - mp + mm) / 4.0;
+}
+
+/* Pi_ab of a state (rho, m) at every node; P[a*3+b] */
+static void momentum_flux(const grid_t *G, const double *rho, double *const *m, double cs2,
+                          double **P)
+{
+    const int dim = G->p->dim;
+    const long N = (long)G->n[0] * G->n[1] * G->n[2];
+    for (long c = 0; c < N; ++c)
+        for (int a = 0; a < dim; ++a)
+            for (int b = 0; b < dim; ++b)
+                P[a * 3 + b][c] = m[a][c] * (m[b][c] / rho[c]) + (a == b ? cs2 * rho[c] : 0.0);
+}
+
+/* sum_b D_b Pi_ab at node (i,j,k) */
+static double div_flux(const grid_t *G, double **P, const nbr_t *nb, int a)
+{
+    double s = 0.0;
+    for (int b = 0; b < G->p->dim; ++b) s += dcen(P[a * 3 + b], nb, b);
+    return s;
+}
+
+int oracle_step_mames(const oracle_params *p, double *rho, double *u, double *v, double *w,
+                      long nsteps)
+{
+    grid_t G;
+    if (setup_grid(p, &G) != 0) return -1;
+    for (int d = 0; d < p->dim; ++d)
+        if (!G.periodic[d]) return -1;
+    if (p->two_phase) return -1;
+    const int dim = p->dim;
+    const long N = (long)G.n[0] * G.n[1] * G.n[2];
+    const double dt = p->dt, nu = p->nu;
+    const double cs2 = (1.0 / dt) * (1.0 / dt) / 3.0;
+    double *vel[3] = {u, v, w};
+    double *m[3] = {0}, *ms[3] = {0}, *P[9] = {0}, *Ps[9] = {0}, *rhos;
+    int ok = (rhos = malloc(sizeof(double) * N)) != NULL;
+    for (int a = 0; a < 3; ++a) {
+        ok &= (m[a] = malloc(sizeof(double) * N)) != NULL;
+        ok &= (ms[a] = malloc(sizeof(double) * N)) != NULL;
+    }
+    for (int q = 0; q < 9; ++q) {
+        ok &= (P[q] = malloc(sizeof(double) * N)) != NULL;
+        ok &= (Ps[q] = malloc(sizeof(double) * N)) != NULL;
+    }
+    if (ok) {
+        for (long step = 0; step < nsteps; ++step) {
+            for (long c = 0; c < N; ++c)
+                for (int a = 0; a < dim; ++a) m[a][c] = rho[c] * vel[a][c];
+            momentum_flux(&G, rho, m, cs2, P);
+            /* predictor, Eqs. (2.6) and (2.7) */
+            for (int k = 0; k < G.n[2]; ++k)
+                for (int j = 0; j < G.n[1]; ++j)
+                    for (int i = 0; i < G.n[0]; ++i) {
+                        nbr_t nb = neighbours(&G, i, j, k);
+                        double div_m = 0.0, ddPi = 0.0;
+                        for (int a = 0; a < dim; ++a) {
+                            div_m += dcen(m[a], &nb, a);
+                            for (int b = 0; b < dim; ++b) ddPi += dmix(&G, P[a * 3 + b], i, j, k, a, b);
+                        }
+                        rhos[nb.c] = rho[nb.c] - dt * div_m + 0.5 * dt * dt * ddPi;
+                        for (int a = 0; a < dim; ++a) {
+                            double grad_div = 0.0;
+                            for (int g = 0; g < dim; ++g) grad_div += dmix(&G, m[g], i, j, k, a, g);
+                            ms[a][nb.c] = m[a][nb.c] - dt * div_flux(&G, P, &nb, a) +
+                                          nu * dt * lap(&G, m[a], &nb) + 2.0 * nu * dt * grad_div;
+                        }
+                    }
+            /* corrector, Eqs. (2.8) and (2.9) */
+            momentum_flux(&G, rhos, ms, cs2, Ps);
+            const double cc = nu / cs2 - 0.5 * dt;
+            for (int k = 0; k < G.n[2]; ++k)
+                for (int j = 0; j < G.n[1]; ++j)
+                    for (int i = 0; i < G.n[0]; ++i) {
+                        nbr_t nb = neighbours(&G, i, j, k);
+                        for (int a = 0; a < dim; ++a) {
+                            double mn = ms[a][nb.c] +
+                                        cc * (div_flux(&G, Ps, &nb, a) - div_flux(&G, P, &nb, a));
+                            vel[a][nb.c] = mn / rhos[nb.c];
+                        }
+                    }
+            memcpy(rho, rhos, sizeof(double) * N);
+        }
+    }
+    free(rhos);
+    for (int a = 0; a < 3; ++a) { free(m[a]); free(ms[a]); }
+    for (int q = 0; q < 9; ++q) { free(P[q]); free(Ps[q]); }
+    return ok ? 0 : -2;
 }
 
 /* Chemical potential field of phi (exposed for the equilibrium pins). */

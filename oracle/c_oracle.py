@@ -62,6 +62,8 @@ def _load():
         lib.oracle_chem_pot.restype = ctypes.c_int
         lib.oracle_grad_lap_iso.argtypes = [P, dp, ctypes.c_int, dp, dp]
         lib.oracle_grad_lap_iso.restype = ctypes.c_int
+        lib.oracle_step_mames.argtypes = [P, dp, dp, dp, dp, ctypes.c_long]
+        lib.oracle_step_mames.restype = ctypes.c_int
         lib.oracle_reduce.argtypes = [P, dp, dp, dp, dp, dp, dp, dp, dp]
         lib.oracle_reduce.restype = ctypes.c_int
         _lib = lib
@@ -109,6 +111,18 @@ def step(p: OracleParams, rho, u, v, w=None, phi=None, nsteps: int = 1):
     if rc != 0:
         raise ValueError(f"oracle_step failed with status {rc}")
     return rho, u, v, w, phi
+
+
+def step_mames(p: OracleParams, rho, u, v, w=None, nsteps: int = 1):
+    """Advance IN PLACE by ``nsteps`` steps of the MAMEs predictor-corrector
+    (Eqs. 2.6-2.9), periodic single-phase grids only."""
+    lib = _load()
+    w = np.zeros(rho.shape) if w is None else w
+    rc = lib.oracle_step_mames(ctypes.byref(p), _ptr(rho), _ptr(u), _ptr(v), _ptr(w),
+                               int(nsteps))
+    if rc != 0:
+        raise ValueError(f"oracle_step_mames failed with status {rc}")
+    return rho, u, v, w
 
 
 def chem_pot(p: OracleParams, phi):

@@ -537,6 +537,133 @@ def test_capillary_wave_period_oracle(oracle_lib):
     assert ta.local_extrema(ts, hs, "min")[0] == pytest.approx(period / 2, rel=0.06)
 
 
+# ------------------------------------------- MAMEs comparison scheme (f4)
+@pytest.mark.parametrize("shape", [(12, 10), (6, 7, 8)])
+def test_mames_conserves_mass_and_momentum(oracle_lib, shape):
+    """Eqs. 2.6-2.9 on a periodic grid: every spatial operator is a
+    difference that telescopes, so sum(rho) and sum(rho u) are conserved to
+    rounding."""
+    co = oracle_lib
+    rng = np.random.default_rng(11)
+    rho = 1 + 0.01 * _smooth(rng, shape)
+    vel = [0.05 * _smooth(rng, shape) for _ in range(len(shape))]
+    p = co.make_params(shape, nu=0.05)
+    st = [rho.copy()] + [x.copy() for x in vel]
+    m0 = [float((st[0] * x).sum()) for x in st[1:]]
+    s0 = float(st[0].sum())
+    w = st[3] if len(shape) == 3 else None
+    co.step_mames(p, st[0], st[1], st[2], w, nsteps=20)
+    assert abs(st[0].sum() - s0) < 1e-12 * s0
+    for a, x in enumerate(st[1:]):
+        assert abs((st[0] * x).sum() - m0[a]) < 1e-13 * rho.size
+
+
+def test_mames_shear_wave_exact_decay(oracle_lib):
+    """A shear wave u = u0 sin(k y) has Pi_xy = 0, no pressure gradient and
+    no divergence, so the predictor only diffuses it and the corrector adds
+    nothing: u decays by exactly (1 - 4 nu dt sin^2(k/2)) per step."""
+    co = oracle_lib
+    n, u0, nu = 32, 0.02, 0.07
+    k = 2 * math.pi * 3 / n
+    y = np.arange(n)
+    u = np.tile((u0 * np.sin(k * y))[:, None], (1, 20))
+    rho = np.ones_like(u)
+    v = np.zeros_like(u)
+    p = co.make_params(u.shape, nu=nu)
+    co.step_mames(p, rho, u, v, nsteps=50)
+    g = (1 - 4 * nu * math.sin(k / 2) ** 2) ** 50
+    assert np.abs(u - g * u0 * np.sin(k * y)[:, None]).max() < 1e-15
+    assert np.abs(rho - 1).max() == 0.0
+
+
+@pytest.mark.parametrize("dt,nu", [(1.0, 0.1), (0.5, 0.02)])
+def test_mames_linear_plane_wave_symbol(oracle_lib, dt, nu):
+    """Linearised about rest (rho = 1 + eps rho~, u = eps u~), one step of
+    Eqs. 2.6-2.9 maps a plane wave exp(i k.x) through the Fourier symbols of
+    the centred operators: D_a -> i sin k_a, D_aa -> 2 cos k_a - 2,
+    D_ab -> -sin k_a sin k_b (a != b).  Predictor:
+      rho* = rho - dt i s.m + (dt^2/2) c_s^2 (c_x + c_y) rho,
+      m*_a = m_a - dt c_s^2 i s_a rho + nu dt (c_x + c_y) m_a + 2 nu dt sum_g X_ag m_g;
+    corrector: m_a += (nu/c_s^2 - dt/2) c_s^2 i s_a (rho* - rho).  A wave of
+    amplitude 1e-6 follows this to 1e-5 relative (the O(eps^2) terms).  Pins
+    every coefficient of the scheme, the sign of the mixed derivative and the
+    use of rho* in the corrector."""
+    co = oracle_lib
+    ny, nx = 12, 16
+    kx, ky = 2 * math.pi * 1 / nx, 2 * math.pi * 2 / ny
+    X, Y = np.meshgrid(np.arange(nx), np.arange(ny))
+    E = np.exp(1j * (kx * X + ky * Y))
+    a = np.array([0.3 + 0.2j, -0.5 + 0.4j, 0.1 - 0.7j])   # rho~, u~, v~
+    eps = 1e-6
+    rho = 1 + eps * np.real(a[0] * E)
+    u = eps * np.real(a[1] * E)
+    v = eps * np.real(a[2] * E)
+    p = co.make_params((ny, nx), dt=dt, nu=nu)
+    co.step_mames(p, rho, u, v, nsteps=1)
+    amp = lambda f: 2.0 / f.size * (f * np.conj(E)).sum() / eps
+    got = np.array([amp(rho - 1), amp(u), amp(v)])
+    cs2 = (1 / dt) ** 2 / 3
+    s = np.array([math.sin(kx), math.sin(ky)])
+    c = np.array([2 * math.cos(kx) - 2, 2 * math.cos(ky) - 2])
+    X2 = np.array([[c[0], -s[0] * s[1]], [-s[0] * s[1], c[1]]])
+    r0, m0 = a[0], a[1:]
+    rs = r0 - dt * 1j * (s @ m0) + 0.5 * dt * dt * cs2 * c.sum() * r0
+    ms = m0 - dt * cs2 * 1j * s * r0 + nu * dt * c.sum() * m0 + 2 * nu * dt * (X2 @ m0)
+    mn = ms + (nu / cs2 - 0.5 * dt) * cs2 * 1j * s * (rs - r0)
+    want = np.array([rs, mn[0], mn[1]])
+    assert np.abs(got - want).max() < 1e-5 * np.abs(want).max()
+    # the symbol is not trivial: each coefficient moves the answer
+    assert np.abs(want - a).max() > 1e-2
+
+
+@pytest.mark.slow
+def test_mames_vs_smames_tgv_errors_paper(oracle_lib):
+    """Section 3.1 (Re = 20, N_L = 50, c = 20, 0 <= t <= 8): both schemes
+    stay near 1e-3 early (t = 1); at t = 8 the simplified scheme is still
+    O(1e-3) while the MAMEs have drifted to O(1e-2)."""
+    co = oracle_lib
+    n, c = 100, 20.0
+    L, u0 = n / 2, 1.0 / c
+    nu = u0 * L / 20.0
+    tc = int(L / u0)
+    err = {}
+    for name, stepper in (("smames", co.step), ("mames", co.step_mames)):
+        rho, u, v = wl.tgv2d(n, u0)
+        p = co.make_params((n, n), nu=nu)
+        out, done = [], 0
+        for t in (1, 8):
+            stepper(p, rho, u, v, nsteps=t * tc - done)
+            done = t * tc
+            ue, _ = wl.tgv2d_exact(n, u0, nu, done)
+            out.append(rel_l2(u, ue))
+        err[name] = out
+    assert err["smames"][0] < 2e-3 and err["mames"][0] < 2e-3
+    assert 5e-4 < err["smames"][1] < 5e-3
+    assert 3e-3 < err["mames"][1] < 3e-2
+    assert err["mames"][1] > 3 * err["smames"][1]
+
+
+@pytest.mark.parametrize("n,c", [(40, 6.0), (100, 16.0)])
+def test_mames_stability_region_is_smaller(oracle_lib, n, c):
+    """Section 3.1 stability diagram (Re = 20): on the same grid the
+    simplified scheme runs stably at a larger time step than the MAMEs, and
+    the gap widens with N_L.  Here N_L = 20, c = 6 and N_L = 50, c = 16 are
+    stable for the simplified scheme and blow up for the MAMEs (its limits
+    found here: c = 8 and c = 20; the simplified scheme's: 5 and 12)."""
+    co = oracle_lib
+    L, u0 = n / 2, 1.0 / c
+    nu = u0 * L / 20.0
+    steps = int(2 * L / u0)
+    res = {}
+    for name, stepper in (("smames", co.step), ("mames", co.step_mames)):
+        rho, u, v = wl.tgv2d(n, u0)
+        p = co.make_params((n, n), nu=nu)
+        with np.errstate(all="ignore"):
+            stepper(p, rho, u, v, nsteps=steps)
+        res[name] = bool(np.isfinite(u).all() and np.abs(u).max() < 10 * u0)
+    assert res == {"smames": True, "mames": False}
+
+
 # ---------------------------------------------------------------- cross-check
 @pytest.mark.parametrize("shape", [(8, 8), (6, 5, 7)])
 @pytest.mark.parametrize("two_phase", [False, True])
