@@ -435,6 +435,94 @@ def run_subdomains(args):
     return 0
 
 
+def run_mames(args):
+    """The simplified one-step scheme against the MAMEs predictor-corrector it
+    replaces (Section 3), both as fused GPU kernels: (a) the paper's DPSL run
+    (320^2, 16000 steps, FP64) wall time, the paper's own comparison (258.6 s
+    vs 365.5 s on a CPU); (b) throughput on a 4096^2 periodic TGV in FP32
+    (inputs larger than L2); (c) the 2D TGV error at t = 8 (Re = 20,
+    N_L = 50, c = 20, FP64), O(1e-3) vs O(1e-2) in the paper."""
+    import numpy as np
+    import torch
+    from paper_2012_03525_gb300 import acm, build
+    from paper_2012_03525_gb300 import workloads as wl
+    build.build()
+    schemes = {"smames": acm.SCHEME_SMAMES, "mames": acm.SCHEME_MAMES}
+    out = {k: {} for k in schemes}
+    stream = torch.cuda.Stream()
+
+    def timed(solver, steps):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        solver.step(steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        solver.sync()
+        return ev0.elapsed_time(ev1) / 1e3
+
+    # (a) DPSL, FP64, end to end through the API (fields read back)
+    n, nt = 320, 16000
+    us, nu = wl.dpsl_lattice(n, nt)
+    rho, u, v = wl.dpsl(n)
+    for name, sc in schemes.items():
+        s = acm.Solver(acm.make_params((n, n), nu=nu, scheme=sc))
+        s.set_stream(stream.cuda_stream)
+        s.set_fields(rho, u * us, v * us)
+        s.step(64)
+        s.sync()
+        s.set_fields(rho, u * us, v * us)
+        t0 = time.perf_counter()
+        s.step(nt)
+        f = s.fields()
+        secs = time.perf_counter() - t0
+        w = (np.roll(f[2], -1, 1) - np.roll(f[2], 1, 1) - np.roll(f[1], -1, 0) +
+             np.roll(f[1], 1, 0)) * 0.5 * n / us
+        out[name]["dpsl_fp64_seconds"] = secs
+        out[name]["dpsl_enstrophy_t1"] = float(0.5 * (w * w).mean())
+        s.close()
+    # (b) 4096^2 TGV, FP32, device-timed
+    n2 = 4096
+    rho, u, v = wl.tgv2d(n2, 0.05)
+    for name, sc in schemes.items():
+        s = acm.Solver(acm.make_params((n2, n2), nu=0.01, precision=acm.FP32_DEV, scheme=sc))
+        s.set_stream(stream.cuda_stream)
+        s.set_fields(rho, u, v)
+        s.step(max(args.warmup, 64))
+        secs = timed(s, args.steps)
+        out[name]["tgv4096_fp32_GLUPS"] = n2 * n2 * args.steps / secs / 1e9
+        out[name]["tgv4096_fp32_hbm_frac"] = (24 * n2 * n2 * args.steps / secs / 1e9 /
+                                              measured_peaks()[0])
+        s.close()
+    # (c) Section 3.1 accuracy
+    n3, c = 100, 20.0
+    L, u0 = n3 / 2, 1.0 / c
+    nu3 = u0 * L / 20.0
+    steps3 = int(8 * L / u0)
+    rho, u, v = wl.tgv2d(n3, u0)
+    ue, _ = wl.tgv2d_exact(n3, u0, nu3, steps3)
+    for name, sc in schemes.items():
+        s = acm.Solver(acm.make_params((n3, n3), nu=nu3, scheme=sc))
+        s.set_fields(rho, u, v)
+        s.step(steps3)
+        g = s.fields()[1]
+        out[name]["tgv_re20_Er_u_t8"] = float(np.sqrt(((g - ue) ** 2).sum() / (ue ** 2).sum()))
+        s.close()
+    ratio = out["mames"]["dpsl_fp64_seconds"] / out["smames"]["dpsl_fp64_seconds"]
+    print(json.dumps({
+        "metric": "DPSL wall time, MAMEs / simplified", "value": ratio, "unit": "ratio",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "simplified one-step scheme vs MAMEs predictor-corrector: DPSL "
+                               "320^2 x 16000 steps FP64; TGV 4096^2 FP32; TGV Re=20 accuracy"},
+        "runs": out,
+        "paper_context": {"dpsl_seconds": {"smames": 258.6, "mames": 365.5},
+                          "tgv_seconds": {"smames": 18.0, "mames": 23.3},
+                          "hardware": "unnamed CPU (paper, Sections 3.1 and 3.3)"},
+    }))
+    return 0
+
+
 def run_dpsl(args):
     """The paper's doubly periodic shear layer (Section 3.3: N_L = 320,
     N_t = 16000, Re = 1e4, 0 <= t <= 1) timed end to end on the GPU in FP64
@@ -483,7 +571,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="tgv3d", choices=["tgv3d", "drops", "closure", "dpsl", "subdomains"],
+    ap.add_argument("--workload", default="tgv3d", choices=["tgv3d", "drops", "closure", "dpsl", "subdomains", "mames"],
                     help="tgv3d: the bench line; drops: the batched two-phase workload; "
                          "closure: the learned closure's time-to-eps comparison")
     ap.add_argument("--train-trajectories", type=int, default=32)
@@ -509,6 +597,8 @@ def main():
         return run_dpsl(args)
     if args.workload == "subdomains":
         return run_subdomains(args)
+    if args.workload == "mames":
+        return run_mames(args)
 
     import numpy as np
     import torch

@@ -92,7 +92,15 @@ typedef struct {
     double theta_deg;   /* two-phase contact angle of wall faces (degrees):
                            d_n phi = -(2/W) cos(theta) (1 - phi_w^2), d_n mu = 0
                            (Section 2); 90 = neutral wetting */
+    int scheme;         /* ACM_SCHEME_SMAMES: the one-step update, Eqs.
+                           (2.10)-(2.11); ACM_SCHEME_MAMES: the predictor-
+                           corrector of Eqs. (2.6)-(2.9) that it replaces
+                           (comparison scheme: 2D, periodic, single-phase,
+                           no body force; sat_mask is ignored) */
 } acm_params;
+
+/* time-stepping scheme */
+enum { ACM_SCHEME_SMAMES = 0, ACM_SCHEME_MAMES = 1 };
 
 /* Supported combinations (others return ACM_EINVAL):
  *   dim 2: periodic, wall or lid faces; single- or two-phase (walls of

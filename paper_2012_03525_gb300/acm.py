@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(_HERE, "libacm.so")
 OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5, -6
 BC_PERIODIC, BC_WALL, BC_LID, BC_HALO = 0, 1, 2, 3
 FP64, FP32_DEV = 0, 1
+SCHEME_SMAMES, SCHEME_MAMES = 0, 1
 TUNE_ZCHUNKS, TUNE_T3Y, TUNE_GRAPH_STEPS, TUNE_BLOCKS = 1, 2, 3, 4
 
 #: every symbol include/acm.h declares (checked by the CPU tests)
@@ -45,6 +46,7 @@ class Params(ctypes.Structure):
         ("sigma", ctypes.c_double), ("W", ctypes.c_double), ("M", ctypes.c_double),
         ("precision", ctypes.c_int), ("sat_mask", ctypes.c_int),
         ("theta_deg", ctypes.c_double),
+        ("scheme", ctypes.c_int),
     ]
 
 
@@ -115,7 +117,7 @@ def load():
 
 def make_params(shape, dt=1.0, nu=0.01, rho0=1.0, bc=None, lid_u=(0, 0, 0), g=(0, 0, 0),
                 two_phase=False, sigma=0.0, W=4.0, M=0.0, precision=FP64, sat_mask=3,
-                theta_deg=90.0) -> Params:
+                theta_deg=90.0, scheme=SCHEME_SMAMES) -> Params:
     """``shape`` is (ny, nx) for 2D or (nz, ny, nx) for 3D (array order)."""
     p = Params()
     if len(shape) == 2:
@@ -134,6 +136,7 @@ def make_params(shape, dt=1.0, nu=0.01, rho0=1.0, bc=None, lid_u=(0, 0, 0), g=(0
     p.precision = precision
     p.sat_mask = sat_mask
     p.theta_deg = theta_deg
+    p.scheme = scheme
     return p
 
 

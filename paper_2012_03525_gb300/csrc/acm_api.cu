@@ -16,6 +16,7 @@ using namespace acm;
 
 struct acm_handle {
     int nruns = 0, dim = 2, prec = ACM_FP64, two_phase = 0, any_wall = 0;
+    int scheme = ACM_SCHEME_SMAMES;
     std::vector<acm_params> params;
     std::vector<RunDesc> runs;
     std::vector<long long> npoints;   // nodes per run
@@ -114,6 +115,14 @@ acm_status validate(const acm_params &p, std::string &why)
                 return bad("3D grids support periodic faces only (z: periodic or ACM_BC_HALO)");
         if (p.nx < 2 || p.ny < 2) return bad("3D grids need nx, ny >= 2");
         if (p.two_phase) return bad("two-phase runs are 2D only");
+    }
+    if (p.scheme != ACM_SCHEME_SMAMES && p.scheme != ACM_SCHEME_MAMES) return bad("unknown scheme");
+    if (p.scheme == ACM_SCHEME_MAMES) {
+        if (p.dim != 2 || p.two_phase) return bad("the MAMEs scheme is 2D single-phase only");
+        for (int f = 0; f < 4; ++f)
+            if (p.bc[f] != ACM_BC_PERIODIC) return bad("the MAMEs scheme needs periodic faces");
+        if (p.g[0] != 0.0 || p.g[1] != 0.0 || p.g[2] != 0.0)
+            return bad("the MAMEs scheme takes no body force");
     }
     if (p.two_phase) {
         if (!(p.W > 0) || !(p.sigma >= 0) || !(p.M >= 0)) return bad("bad sigma/W/M");
@@ -288,8 +297,10 @@ acm_status create_common(const acm_params *params, int nruns, acm_handle **out)
     } else if (nruns > 1) {
         for (int r = 1; r < nruns; ++r) {
             const acm_params &p = params[r];
-            if (p.dim != p0.dim || p.precision != p0.precision || p.two_phase != p0.two_phase)
-                return fail(nullptr, ACM_EINVAL, "batch runs must share dim, precision, two_phase");
+            if (p.dim != p0.dim || p.precision != p0.precision || p.two_phase != p0.two_phase ||
+                p.scheme != p0.scheme)
+                return fail(nullptr, ACM_EINVAL,
+                            "batch runs must share dim, precision, two_phase, scheme");
         }
     }
     acm_handle *h = new (std::nothrow) acm_handle();
@@ -298,6 +309,7 @@ acm_status create_common(const acm_params *params, int nruns, acm_handle **out)
     h->dim = p0.dim;
     h->prec = p0.precision;
     h->two_phase = p0.two_phase;
+    h->scheme = p0.scheme;
     h->params.assign(params, params + nruns);
     h->have_fields.assign(nruns, 0);
     auto bail = [&](acm_status st) {
@@ -385,6 +397,10 @@ acm_status create_common(const acm_params *params, int nruns, acm_handle **out)
     if (h->dim == 2) {
         if (h->prec == ACM_FP64) step2d_max_blocks_per_sm<double>(h->two_phase);
         else step2d_max_blocks_per_sm<float>(h->two_phase);
+        if (h->scheme == ACM_SCHEME_MAMES) {
+            if (h->prec == ACM_FP64) mames2d_max_blocks_per_sm<double>();
+            else mames2d_max_blocks_per_sm<float>();
+        }
     } else {
         for (int t3y : {8, 16}) {
             if (h->prec == ACM_FP64) step3d_max_blocks_per_sm<double>(t3y);
@@ -432,6 +448,11 @@ cudaError_t one_step(acm_handle *h, int from)
         return e;
     }
     int blocks = h->tune.blocks;
+    if (h->scheme == ACM_SCHEME_MAMES) {
+        if (blocks <= 0) blocks = h->sms * mames2d_max_blocks_per_sm<T>();
+        return launch_mames2d<T>(h->druns, h->dwork, h->nwork, in, out, h->derr, blocks,
+                                 h->stream);
+    }
     if (blocks <= 0) blocks = h->sms * step2d_max_blocks_per_sm<T>(h->two_phase);
     return launch_step2d<T>(h->druns, h->dwork, h->nwork, h->two_phase, in, out, h->derr, blocks,
                             h->stream);
@@ -664,8 +685,13 @@ acm_status acm_autotune(acm_handle *h, int nsteps, double *best_ms_per_step)
                 if (!dup) cands.push_back({t3y, zc, 0});
             }
     } else {
-        const int per_sm = h->prec == ACM_FP64 ? step2d_max_blocks_per_sm<double>(h->two_phase)
-                                               : step2d_max_blocks_per_sm<float>(h->two_phase);
+        const bool mames = h->scheme == ACM_SCHEME_MAMES;
+        const int per_sm =
+            h->prec == ACM_FP64
+                ? (mames ? mames2d_max_blocks_per_sm<double>()
+                         : step2d_max_blocks_per_sm<double>(h->two_phase))
+                : (mames ? mames2d_max_blocks_per_sm<float>()
+                         : step2d_max_blocks_per_sm<float>(h->two_phase));
         for (int k = 1; k <= per_sm; ++k) cands.push_back({h->tune.t3y, 0, k * h->sms});
     }
 

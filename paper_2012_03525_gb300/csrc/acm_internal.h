@@ -104,6 +104,14 @@ cudaError_t launch_reduce(const RunDesc *druns, int nruns, int dim, Fields<T> cu
                           const T *pv, const T *pw, double *dpartials, int blocks_per_run,
                           double *dout, cudaStream_t s);
 
+// The MAMEs predictor-corrector (comparison scheme), periodic 2D runs over
+// the same (run, tile) work list as launch_step2d.
+template <typename T>
+cudaError_t launch_mames2d(const RunDesc *druns, const int4 *dwork, int nwork, Fields<T> in,
+                           Fields<T> out, unsigned *derr, int blocks, cudaStream_t s);
+template <typename T>
+int mames2d_max_blocks_per_sm();
+
 // Halo exchange of 3D sub-domains (runs 0..nruns-1 form a ring along z):
 // copies the two boundary planes of every run into the ghost planes of its
 // neighbours, all four fields of f, one launch.

@@ -60,6 +60,11 @@ def test_params_struct_layout_matches_header():
     (dict(shape=(4, 8, 8), bc=[0, 0, 0, 0, 3, 0]), "both faces"),
     (dict(shape=(1, 8, 8), bc=[0, 0, 0, 0, 3, 3]), "nz >= 2"),
     (dict(shape=(4, 8, 8), bc=[3, 3, 0, 0, 0, 0]), "z faces of 3D"),
+    (dict(shape=(8, 8), scheme=5), "unknown scheme"),
+    (dict(shape=(4, 8, 8), scheme=1), "MAMEs"),
+    (dict(shape=(8, 8), scheme=1, two_phase=True), "MAMEs"),
+    (dict(shape=(8, 8), scheme=1, bc=[1, 1, 0, 0, 0, 0]), "MAMEs"),
+    (dict(shape=(8, 8), scheme=1, g=(1e-5, 0, 0)), "MAMEs"),
 ])
 def test_invalid_params_rejected_on_host(lib, kw, msg):
     shape = kw.pop("shape")
