@@ -105,8 +105,10 @@ enum { ACM_SCHEME_SMAMES = 0, ACM_SCHEME_MAMES = 1 };
 /* Supported combinations (others return ACM_EINVAL):
  *   dim 2: periodic, wall or lid faces; single- or two-phase (walls of
  *          two-phase runs carry the wetting condition); FP64 or FP32_DEV;
- *   dim 3: periodic faces (x, y; z periodic or ACM_BC_HALO on both z
- *          faces), single-phase; FP64 or FP32_DEV.                    */
+ *   dim 3: periodic x and y faces; single-phase with z periodic or
+ *          ACM_BC_HALO on both z faces; two-phase (D3Q19 isotropic
+ *          operators) with z periodic or walls on both z faces (wetting
+ *          condition, stationary); FP64 or FP32_DEV.                 */
 
 /* Create a solver for ONE grid.  Validates the parameters, allocates the
  * double-buffered device fields on the current CUDA device and returns the

@@ -44,6 +44,7 @@ struct acm_handle {
     // from and joined back into `stream` with events
     std::vector<cudaStream_t> side;
     std::vector<cudaEvent_t> ev;    // [0] fork, [r] join of slab r
+    void *scratch[3] = {};          // 3D two-phase: mu, phi*, Delta rho
     cudaGraphExec_t gexec = nullptr;
     Tuning tune;
     std::string err;
@@ -110,11 +111,14 @@ acm_status validate(const acm_params &p, std::string &why)
         if (lo != ACM_BC_PERIODIC && n[d] < 4) return bad("walls need >= 4 nodes across");
     }
     if (p.dim == 3) {
-        for (int f = 0; f < 6; ++f)
-            if (p.bc[f] != ACM_BC_PERIODIC && !(f >= 4 && p.bc[f] == ACM_BC_HALO))
-                return bad("3D grids support periodic faces only (z: periodic or ACM_BC_HALO)");
+        for (int f = 0; f < 4; ++f)
+            if (p.bc[f] != ACM_BC_PERIODIC) return bad("3D grids need periodic x and y faces");
+        const int zb = p.bc[4];
+        if (zb == ACM_BC_LID) return bad("3D grids have no lid faces");
+        if (zb == ACM_BC_WALL && !p.two_phase)
+            return bad("3D z walls are supported for two-phase runs only");
+        if (zb == ACM_BC_HALO && p.two_phase) return bad("3D sub-domains are single-phase only");
         if (p.nx < 2 || p.ny < 2) return bad("3D grids need nx, ny >= 2");
-        if (p.two_phase) return bad("two-phase runs are 2D only");
     }
     if (p.scheme != ACM_SCHEME_SMAMES && p.scheme != ACM_SCHEME_MAMES) return bad("unknown scheme");
     if (p.scheme == ACM_SCHEME_MAMES) {
@@ -260,6 +264,8 @@ void release(acm_handle *h)
     if (h->dout) cudaFree(h->dout);
     if (h->dstage) cudaFree(h->dstage);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    for (void *p : h->scratch)
+        if (p) cudaFree(p);
     for (cudaStream_t st : h->side) cudaStreamDestroy(st);
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
 }
@@ -378,6 +384,11 @@ acm_status create_common(const acm_params *params, int nruns, acm_handle **out)
                 CKB(cudaMalloc(&h->buf[b][f], h->pool * h->esize()));
                 CKB(cudaMemset(h->buf[b][f], 0, h->pool * h->esize()));
             }
+    if (h->dim == 3 && h->two_phase)
+        for (void *&p : h->scratch) {
+            CKB(cudaMalloc(&p, h->pool * h->esize()));
+            CKB(cudaMemset(p, 0, h->pool * h->esize()));
+        }
     CKB(cudaMalloc(&h->druns, sizeof(RunDesc) * nruns));
     CKB(cudaMemcpy(h->druns, h->runs.data(), sizeof(RunDesc) * nruns, cudaMemcpyHostToDevice));
     if (!work.empty()) {
@@ -423,6 +434,10 @@ template <typename T>
 cudaError_t one_step(acm_handle *h, int from)
 {
     Fields<T> in = fields_of<T>(h, from), out = fields_of<T>(h, 1 - from);
+    if (h->dim == 3 && h->two_phase)
+        return launch_tp3d<T>(h->runs[0], in, out, static_cast<T *>(h->scratch[0]),
+                              static_cast<T *>(h->scratch[1]), static_cast<T *>(h->scratch[2]),
+                              h->derr, h->sms, h->stream);
     if (h->dim == 3) {
         cudaError_t e = cudaSuccess;
         if (h->halo) {

@@ -104,6 +104,12 @@ cudaError_t launch_reduce(const RunDesc *druns, int nruns, int dim, Fields<T> cu
                           const T *pv, const T *pw, double *dpartials, int blocks_per_run,
                           double *dout, cudaStream_t s);
 
+// 3D two-phase step (five launches: mu, Delta rho, momentum + phi*, mu*,
+// phi^{n+1}); mu, phs, dr are scratch fields of the run's storage size.
+template <typename T>
+cudaError_t launch_tp3d(const RunDesc &R, Fields<T> in, Fields<T> out, T *mu, T *phs, T *dr,
+                        unsigned *err, int sms, cudaStream_t s);
+
 // The MAMEs predictor-corrector (comparison scheme), periodic 2D runs over
 // the same (run, tile) work list as launch_step2d.
 template <typename T>

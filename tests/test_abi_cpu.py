@@ -51,7 +51,10 @@ def test_params_struct_layout_matches_header():
     (dict(shape=(8, 8), nu=-1.0), "nu"),
     (dict(shape=(8, 8), bc=[1, 0, 0, 0, 0, 0]), "periodic"),
     (dict(shape=(3, 8), bc=[0, 0, 1, 1, 0, 0]), "walls"),
-    (dict(shape=(4, 8, 8), bc=[1, 1, 0, 0, 0, 0]), "3D"),
+    (dict(shape=(4, 8, 8), bc=[1, 1, 0, 0, 0, 0]), "periodic x and y"),
+    (dict(shape=(4, 8, 8), bc=[0, 0, 0, 0, 1, 1]), "two-phase runs only"),
+    (dict(shape=(4, 8, 8), bc=[0, 0, 0, 0, 2, 2], two_phase=True), "lid"),
+    (dict(shape=(4, 8, 8), bc=[0, 0, 0, 0, 3, 3], two_phase=True), "single-phase only"),
     (dict(shape=(8, 8), two_phase=True, W=0.0), "sigma/W/M"),
     (dict(shape=(8, 8), two_phase=True, theta_deg=float("nan")), "contact angle"),
     (dict(shape=(8, 8), sat_mask=4), "sat_mask"),

@@ -1,0 +1,139 @@
+"""3D two-phase runs on the GPU (D3Q19 isotropic operators; x, y periodic; z
+periodic or wetting walls): parity with the oracle in FP64 (1e-12) and FP32,
+and the physics the oracle pins fix: the Laplace law of a static 3D drop
+(mu0 = sigma / R) and a drop on a wall moving toward its contact angle."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2012_03525_gb300 import acm, build
+from test_parity_gpu import assert_parity, rel_l2, run_both
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    acm.load()
+
+
+def _drop3d(shape, R, centre, W=4.0, eps=0.0):
+    nz, ny, nx = shape
+    Z, Y, X = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    dx, dy, dz = X - centre[2], Y - centre[1], Z - centre[0]
+    r = np.sqrt(dx ** 2 + (dy * (1 + eps)) ** 2 + dz ** 2)
+    return -np.tanh(2.0 * (r - R) / W)
+
+
+def _state(shape, phi, amp=2e-3, walls=False):
+    nz, ny, nx = shape
+    Z, Y, X = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    u = amp * np.sin(2 * np.pi * Y / ny) * np.cos(2 * np.pi * X / nx)
+    v = amp * np.cos(2 * np.pi * Z / nz) * np.sin(2 * np.pi * X / nx)
+    w = amp * np.sin(2 * np.pi * X / nx) * np.cos(2 * np.pi * Y / ny)
+    if walls:
+        for a in (u, v, w):
+            a[0] = 0.0
+            a[-1] = 0.0
+    return [np.ones(shape), u, v, w, phi]
+
+
+@pytest.mark.parametrize("shape,bc,theta", [
+    ((20, 24, 28), [0] * 6, 90.0),
+    ((17, 22, 33), [0, 0, 0, 0, 1, 1], 60.0),
+    ((16, 20, 24), [0, 0, 0, 0, 1, 1], 150.0),
+])
+def test_two_phase_3d_fp64(oracle_lib, shape, bc, theta):
+    walls = bc[4] == 1
+    centre = (0.0 if walls else shape[0] / 2, shape[1] / 2 - 0.3, shape[2] / 2 + 0.2)
+    phi = _drop3d(shape, 7.0, centre, eps=0.1)
+    st = _state(shape, phi, walls=walls)
+    sigma, nu = 1e-2, 0.1
+    ref, got = run_both(oracle_lib, shape, st, 60, nu=nu, bc=bc, two_phase=True, sigma=sigma,
+                        W=4.0, M=0.3, theta_deg=theta, g=(0.0, 0.0, -1e-6))
+    assert_parity(ref, got, vscale=sigma / nu)
+
+
+def test_two_phase_3d_fp32(oracle_lib):
+    shape, bc = (17, 22, 33), [0, 0, 0, 0, 1, 1]
+    phi = _drop3d(shape, 7.0, (0.0, 11.0, 16.0))
+    st = _state(shape, phi, walls=True)
+    ref, got = run_both(oracle_lib, shape, st, 100, gpu_kw={"precision": acm.FP32_DEV}, nu=0.1,
+                        bc=bc, two_phase=True, sigma=1e-2, W=4.0, M=0.3, theta_deg=120.0)
+    assert rel_l2(got[4], ref[4]) < 1e-6
+    for k in (1, 2, 3):
+        assert rel_l2(got[k], ref[k]) < 1e-4
+    assert rel_l2(got[0] - 1, ref[0] - 1) < 1e-3
+
+
+def _relaxed_mu_ratio(n, R, W, sigma, steps):
+    """Relax a static drop; return (mu_core / (sigma / R_eff), mu averaged
+    over the interface / mu_core, max |u|)."""
+    c = (n - 1) / 2
+    phi = _drop3d((n, n, n), R, (c, c, c), W)
+    p = acm.make_params((n, n, n), dt=0.5, nu=0.1, two_phase=True, sigma=sigma, W=W, M=2.0)
+    with acm.Solver(p) as s:
+        z = np.zeros((n, n, n))
+        s.set_fields(np.ones((n, n, n)), z, z, z, phi)
+        s.step(steps)
+        rho, u, v, w, ph = s.fields()
+    r_eff = (3 * ((1 + ph) / 2).sum() / (4 * math.pi)) ** (1 / 3)
+    a, kappa = 3 * sigma / (4 * W), 3 * sigma * W / 8
+    # mu of the relaxed field with the D3Q19 isotropic Laplacian (NumPy)
+    vel = [(1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)]
+    vel += [(ex, ey, 0) for ex in (1, -1) for ey in (1, -1)]
+    vel += [(ex, 0, ez) for ex in (1, -1) for ez in (1, -1)]
+    vel += [(0, ey, ez) for ey in (1, -1) for ez in (1, -1)]
+    lap = np.zeros_like(ph)
+    for e in vel:
+        wgt = 1 / 3 if sum(map(abs, e)) == 1 else 1 / 6
+        lap += wgt * (np.roll(ph, (-e[2], -e[1], -e[0]), axis=(0, 1, 2)) - ph)
+    mu = 4 * a * ph * (ph * ph - 1) - kappa * lap
+    Z, Y, X = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    core = np.sqrt((X - c) ** 2 + (Y - c) ** 2 + (Z - c) ** 2) < r_eff / 2
+    wgt = 1 - ph ** 2
+    mu_core = mu[core].mean()
+    umax = max(np.abs(u).max(), np.abs(v).max(), np.abs(w).max())
+    return mu_core / (sigma / r_eff), (mu * wgt).sum() / wgt.sum() / mu_core, umax
+
+
+def test_laplace_law_static_drop_3d():
+    """A static 3D drop relaxes to uniform mu = mu0 = sigma / R (Gibbs-Thomson:
+    the pressure jump 2 sigma / R over the jump of phi, 2).  The diffuse
+    interface raises mu0 by a term that falls fast with W/R: measured 1.37
+    (W/R = 1/3), 1.17 (1/4), 1.095 (3/16).  Checked here: at W/R = 3/16 mu is
+    uniform to 2 % and within 12 % of sigma/R, and W/R = 1/4 lies further
+    off.  Lattice speed c = 2 (dt = 1/2): at c = 1 the 3D continuity SAT,
+    (1/6) dx^2 Lap(rho) per step, leaves the grid-scale density mode only
+    neutrally stable and the surface-tension force drives it (the oracle
+    blows up there too)."""
+    fine, uniform, umax = _relaxed_mu_ratio(64, 16.0, 3.0, 2e-2, 90000)
+    print(f"3D Laplace W/R=3/16: mu0 ratio {fine:.4f}, uniformity {uniform:.4f}, |u| {umax:.2e}")
+    assert fine == pytest.approx(1.0, abs=0.12)
+    assert uniform == pytest.approx(1.0, abs=0.02)
+    assert umax < 1e-4
+    coarse, _, _ = _relaxed_mu_ratio(64, 16.0, 4.0, 2e-2, 90000)
+    assert coarse - 1.0 > fine - 1.0 > 0.0
+
+
+@pytest.mark.parametrize("theta,direction", [(45.0, -1), (135.0, +1)])
+def test_drop_on_wall_moves_toward_contact_angle_3d(theta, direction):
+    """A hemispherical drop (90 degrees) on a wall of contact angle theta
+    spreads (theta < 90: the height on the axis falls) or dewets (theta > 90:
+    it rises), as in Section 3.6."""
+    shape = (32, 64, 64)
+    R = 14.0
+    phi = _drop3d(shape, R, (0.0, 31.5, 31.5))
+    p = acm.make_params(shape, dt=0.5, nu=0.1, bc=[0, 0, 0, 0, 1, 1], two_phase=True,
+                        sigma=1e-2, W=4.0, M=0.5, theta_deg=theta)
+    with acm.Solver(p) as s:
+        z = np.zeros(shape)
+        s.set_fields(np.ones(shape), z, z, z, phi)
+        s.step(8000)
+        ph = s.fields()[4]
+    col = 0.25 * (ph[:, 31, 31] + ph[:, 32, 31] + ph[:, 31, 32] + ph[:, 32, 32])
+    j = int(np.where(col < 0)[0][0])
+    h = j - 1 + col[j - 1] / (col[j - 1] - col[j])
+    assert direction * (h - R) > 1.0, h
