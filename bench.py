@@ -628,6 +628,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-check", action="store_true",
+                    help="skip the FP64 accuracy run of the tgv3d bench (profiling runs)")
     ap.add_argument("--workload", default="tgv3d", choices=["tgv3d", "drops", "closure", "dpsl", "subdomains", "mames",
                              "twophase3d"],
                     help="tgv3d: the bench line; drops: the batched two-phase workload; "
@@ -723,6 +725,21 @@ def main():
         dist.destroy_process_group()
         return 0
 
+    # accuracy of the FP32 deviation storage: the same K steps in FP64 on the
+    # GPU (outside the timed regions)
+    accuracy = None
+    if not args.no_fp64_check:
+        ref = acm.Solver(acm.make_params((n3, n3, n3), nu=nu, precision=acm.FP64))
+        ref.set_fields(rho, u, v, w)
+        ref.step(args.steps)
+        f64 = ref.fields()[:4]
+        ref.close()
+        f32 = [o.numpy() for o in outs]
+        rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+        accuracy = {"steps": args.steps,
+                    "u_rel_l2_vs_fp64": max(rel(f32[k], f64[k]) for k in (1, 2, 3)),
+                    "rho_dev_rel_l2_vs_fp64": rel(f32[0] - 1.0, f64[0] - 1.0)}
+
     glups = multirank.job_throughput(nodes, args.steps, world, ms / 1e3)
     per_launch_s = ms / 1e3 / args.steps
     peak, peak_kind = measured_peaks()
@@ -753,6 +770,7 @@ def main():
                                                     abs(diag_e2e[0] - mass0)) / mass0),
                         "E_k": float(diag[4]), "max_u": float(diag[6]),
                         "nonfinite": float(diag[7])},
+        "fp32_vs_fp64": accuracy,
     }
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline()

@@ -194,24 +194,38 @@ struct K2 {
 // Eq. (2.10): Delta rho from a node's 7-point neighbourhood (E, W, N, S, U,
 // D), the same operation order for a pair and for a single ring node:
 //   Delta rho = (1/2 cs^2 dt^2) Lap(rho) - (dt/2) [(m_E + m_N + m_U) - (m_W + m_S + m_D)]
-// with m = (rho0 + rho') u_b along each axis b.
-template <typename T>
+// with m = (rho0 + rho') u_b along each axis b.  GEN = false is the
+// instantiation for rho0 = 1 (the paper's reference density) without a body
+// force, where m = rho' u + u is one fused multiply-add.
+template <bool GEN, typename T>
 __device__ __forceinline__ V2<T> delta2(const K2<T> &K, V2<T> rC, V2<T> rE, V2<T> rW, V2<T> rN,
                                         V2<T> rS, V2<T> rU, V2<T> rD, V2<T> uE, V2<T> uW,
                                         V2<T> vN, V2<T> vS, V2<T> wU, V2<T> wD)
 {
-    const V2<T> P = fma2(add2(K.rho0, rE), uE, fma2(add2(K.rho0, rN), vN, mul2(add2(K.rho0, rU), wU)));
-    const V2<T> N = fma2(add2(K.rho0, rW), uW, fma2(add2(K.rho0, rS), vS, mul2(add2(K.rho0, rD), wD)));
+    V2<T> P, N;
+    if (GEN) {
+        P = fma2(add2(K.rho0, rE), uE, fma2(add2(K.rho0, rN), vN, mul2(add2(K.rho0, rU), wU)));
+        N = fma2(add2(K.rho0, rW), uW, fma2(add2(K.rho0, rS), vS, mul2(add2(K.rho0, rD), wD)));
+    } else {
+        P = fma2(rE, uE, fma2(rN, vN, fma2(rU, wU, add2(add2(uE, vN), wU))));
+        N = fma2(rW, uW, fma2(rS, vS, fma2(rD, wD, add2(add2(uW, vS), wD))));
+    }
     const V2<T> lap = fma2(K.m6, rC, add2(add2(add2(rE, rW), add2(rN, rS)), add2(rU, rD)));
     return fma2(K.satc, lap, fma2(K.nhdt, P, mul2(K.hdt, N)));
 }
-template <typename T>
+template <bool GEN, typename T>
 __device__ __forceinline__ T delta1(const K2<T> &K, T rC, T rE, T rW, T rN, T rS, T rU, T rD,
                                     T uE, T uW, T vN, T vS, T wU, T wD)
 {
     const T r0 = K.rho0.x;
-    const T P = fma1(add1(r0, rE), uE, fma1(add1(r0, rN), vN, mul1(add1(r0, rU), wU)));
-    const T N = fma1(add1(r0, rW), uW, fma1(add1(r0, rS), vS, mul1(add1(r0, rD), wD)));
+    T P, N;
+    if (GEN) {
+        P = fma1(add1(r0, rE), uE, fma1(add1(r0, rN), vN, mul1(add1(r0, rU), wU)));
+        N = fma1(add1(r0, rW), uW, fma1(add1(r0, rS), vS, mul1(add1(r0, rD), wD)));
+    } else {
+        P = fma1(rE, uE, fma1(rN, vN, fma1(rU, wU, add1(add1(uE, vN), wU))));
+        N = fma1(rW, uW, fma1(rS, vS, fma1(rD, wD, add1(add1(uW, vS), wD))));
+    }
     const T lap = fma1(K.m6.x, rC, add1(add1(add1(rE, rW), add1(rN, rS)), add1(rU, rD)));
     return fma1(K.satc.x, lap, fma1(K.nhdt.x, P, mul1(K.hdt.x, N)));
 }
@@ -220,7 +234,7 @@ __device__ __forceinline__ T delta1(const K2<T> &K, T rC, T rE, T rW, T rN, T rS
 // rho', u, v, w and Delta rho.  Differences are split into a positive and a
 // negative chain: -hdt (P - N) = fma(-hdt, P, hdt N).  Then
 // u^{n+1} = u + (RHS - Delta rho u) / rho^{n+1}.
-template <typename T, bool GRAV>
+template <typename T, bool GEN>
 __device__ __forceinline__ void node_update2(const V2<T> (&r)[7], const V2<T> (&u)[7],
                                              const V2<T> (&v)[7], const V2<T> (&w)[7],
                                              const V2<T> (&d)[7], const K2<T> &K, V2<T> &rn,
@@ -230,10 +244,16 @@ __device__ __forceinline__ void node_update2(const V2<T> (&r)[7], const V2<T> (&
     P2 mx[7], my[7], mz[7];
 #pragma unroll
     for (int k = 0; k < 7; ++k) {
-        const P2 q = add2(K.rho0, r[k]);
-        mx[k] = mul2(q, u[k]);
-        my[k] = mul2(q, v[k]);
-        mz[k] = mul2(q, w[k]);
+        if (GEN) {
+            const P2 q = add2(K.rho0, r[k]);
+            mx[k] = mul2(q, u[k]);
+            my[k] = mul2(q, v[k]);
+            mz[k] = mul2(q, w[k]);
+        } else {  // rho0 = 1
+            mx[k] = fma2(r[k], u[k], u[k]);
+            my[k] = fma2(r[k], v[k], v[k]);
+            mz[k] = fma2(r[k], w[k], w[k]);
+        }
     }
     auto lap = [&](const P2 (&m)[7]) {
         return fma2(K.m6, m[0], add2(add2(add2(m[1], m[2]), add2(m[3], m[4])), add2(m[5], m[6])));
@@ -255,7 +275,7 @@ __device__ __forceinline__ void node_update2(const V2<T> (&r)[7], const V2<T> (&
     rx = fma2(K.nhsatm, d[1], fma2(K.hsatm, d[2], rx));
     ry = fma2(K.nhsatm, d[3], fma2(K.hsatm, d[4], ry));
     rz = fma2(K.nhsatm, d[5], fma2(K.hsatm, d[6], rz));
-    if (GRAV) {
+    if (GEN) {
         const P2 fb = mul2(K.dt, rho1);
         rx = fma2(fb, K.gx, rx);
         ry = fma2(fb, K.gy, ry);
@@ -316,7 +336,7 @@ __device__ __forceinline__ void store_images(Fields<T> out, long long gi, int gx
         }
 }
 
-template <typename T, int TY, bool GRAV>
+template <typename T, int TY, bool GEN>
 __global__ void __launch_bounds__(T3X *TY / 2, Prec<T>::MINB * 16 / TY)
     k_step3d(const __grid_constant__ CUtensorMap mr, const __grid_constant__ CUtensorMap mu_,
              const __grid_constant__ CUtensorMap mv, const __grid_constant__ CUtensorMap mw,
@@ -419,7 +439,7 @@ __global__ void __launch_bounds__(T3X *TY / 2, Prec<T>::MINB * 16 / TY)
         const T *pr = S + s0 * 4 * PE, *pu = pr + PE, *pv = pr + 2 * PE;
         {   // both own nodes at once (lane x: node a, whose N is node b;
             // lane y: node b, whose S is node a)
-            const P2 dd = delta2<T>(K, mk(C0.r[0], C0.r[1]), mk(pr[ca + 1], pr[cb + 1]),
+            const P2 dd = delta2<GEN, T>(K, mk(C0.r[0], C0.r[1]), mk(pr[ca + 1], pr[cb + 1]),
                                     mk(pr[ca - 1], pr[cb - 1]), mk(C0.r[1], pr[cb + RW]),
                                     mk(pr[ca - RW], C0.r[0]), mk(Cu.r[0], Cu.r[1]),
                                     mk(Cd.r[0], Cd.r[1]), mk(pu[ca + 1], pu[cb + 1]),
@@ -435,7 +455,7 @@ __global__ void __launch_bounds__(T3X *TY / 2, Prec<T>::MINB * 16 / TY)
             const int c = ring_c;
             const T *rd = S + sm * 4 * PE, *wd = rd + 3 * PE;
             const T *ru = S + sp * 4 * PE, *wu = ru + 3 * PE;
-            dw[ring_d] = delta1<T>(K, pr[c], pr[c + 1], pr[c - 1], pr[c + RW], pr[c - RW], ru[c],
+            dw[ring_d] = delta1<GEN, T>(K, pr[c], pr[c + 1], pr[c - 1], pr[c + RW], pr[c - RW], ru[c],
                                    rd[c], pu[c + 1], pu[c - 1], pv[c + RW], pv[c - RW], wu[c],
                                    wd[c]);
         }
@@ -547,7 +567,7 @@ __global__ void __launch_bounds__(T3X *TY / 2, Prec<T>::MINB * 16 / TY)
                              mk(dz[da - RW1], D[S0][0]), mk(D[S1][0], D[S1][1]),
                              mk(D[SM][0], D[SM][1])};
             P2 rn, un, vn, wn;
-            node_update2<T, GRAV>(r, u, v, w, d, K, rn, un, vn, wn);
+            node_update2<T, GEN>(r, u, v, w, d, K, rn, un, vn, wn);
             store2(base_a + (long long)z * PXY, rn.x, un.x, vn.x, wn.x, rn.y, un.y, vn.y, wn.y);
             return true;
         };
@@ -559,16 +579,16 @@ __global__ void __launch_bounds__(T3X *TY / 2, Prec<T>::MINB * 16 / TY)
     }
 }
 
-template <typename T, int TY, bool GRAV>
+template <typename T, int TY, bool GEN>
 int max_blocks_g()
 {
     static int cached = -1;
     if (cached < 0) {
         using G = Geo<T, TY>;
-        cudaFuncSetAttribute(k_step3d<T, TY, GRAV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_step3d<T, TY, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              G::SMEM);
         int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step3d<T, TY, GRAV>, G::NT,
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step3d<T, TY, GEN>, G::NT,
                                                           G::SMEM) != cudaSuccess)
             nb = 1;
         cached = nb > 0 ? nb : 1;
@@ -588,8 +608,9 @@ cudaError_t launch(const CUtensorMap *m, Fields<T> out, const RunDesc &run, unsi
                    int zchunks, int sms, cudaStream_t s)
 {
     using G = Geo<T, TY>;
-    const bool grav = run.g[0] != 0.0 || run.g[1] != 0.0 || run.g[2] != 0.0;
-    const int per_sm = grav ? max_blocks_g<T, TY, true>() : max_blocks_g<T, TY, false>();
+    // the fast instantiation covers rho0 = 1 without a body force
+    const bool gen = run.g[0] != 0.0 || run.g[1] != 0.0 || run.g[2] != 0.0 || run.rho0 != 1.0;
+    const int per_sm = gen ? max_blocks_g<T, TY, true>() : max_blocks_g<T, TY, false>();
     // chunks of zc planes; by default 16 (short enough for many CTAs, long
     // enough that the 4 extra planes per chunk cost little)
     const int nzc = zchunks > 0 ? std::min(zchunks, run.nz) : std::max(1, (run.nz + 15) / 16);
@@ -600,7 +621,7 @@ cudaError_t launch(const CUtensorMap *m, Fields<T> out, const RunDesc &run, unsi
     // resident together work on neighbouring columns at the same depths and
     // share their halo planes through L2
     const long long grid = std::min<long long>(items, (long long)sms * per_sm);
-    if (grav)
+    if (gen)
         k_step3d<T, TY, true><<<(unsigned)grid, G::NT, G::SMEM, s>>>(m[0], m[1], m[2], m[3], out,
                                                                     run, zc, derr);
     else

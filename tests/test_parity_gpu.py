@@ -191,6 +191,23 @@ def test_3d_periodic_random_fp64(oracle_lib, shape, tuning):
     assert_parity(ref, got)
 
 
+@pytest.mark.parametrize("prec", [acm.FP64, acm.FP32_DEV])
+def test_3d_reference_density_not_one(oracle_lib, prec):
+    """rho0 != 1 without a body force takes the general instantiation of the
+    3D step (the fast one assumes rho0 = 1)."""
+    shape = (18, 24, 36)
+    rng = np.random.default_rng(3)
+    rho0 = 2.5
+    state = [rho0 * (1 + 0.01 * _smooth(rng, shape, 6))] + [0.04 * _smooth(rng, shape, 6)
+                                                            for _ in range(3)]
+    ref, got = run_both(oracle_lib, shape, state, 60, gpu_kw={"precision": prec}, nu=0.05,
+                        rho0=rho0)
+    if prec == acm.FP64:
+        assert_parity(ref, got, rho0=rho0)
+    else:
+        assert_parity(ref, got, rho0=rho0, tol=2e-5, tol_rho=1e-4)
+
+
 def test_3d_tgv_fp32_deviation(oracle_lib):
     """FP32 deviation storage against the FP64 oracle on a 48^3 TGV."""
     n = 48
