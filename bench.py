@@ -580,6 +580,63 @@ def run_twophase3d(args):
     return 0
 
 
+def run_cavity(args):
+    """Lid-driven cavity 1024^2, lid speed 0.1, Re = 1000 (walls on the first
+    and last rows/columns, lid on the top row), from rest to the steady
+    state of Section 3.2's criterion max | |u|^{n+1} - |u|^n | < 1e-9 per
+    step, in FP64 and in FP32 deviation storage: steps and wall time to the
+    criterion and the FP32 steady state's error against the FP64 one.  FP32
+    resolves changes of u only down to its rounding (7.5e-9 at 0.1): its run
+    stops at the criterion or after as many steps as the FP64 run took."""
+    import numpy as np
+    import torch
+    from paper_2012_03525_gb300 import acm, build
+    from paper_2012_03525_gb300 import workloads as wl
+    build.build()
+    n, lid, re = 1024, 0.1, 1000.0
+    nu = wl.cavity_nu(n, lid, re)
+    rho, u, v = wl.cavity2d(n, lid)
+    chunk, max_steps, max_seconds = 4000, 4_000_000, 240.0
+    out, fields = {}, {}
+    for name, prec in (("fp64", acm.FP64), ("fp32", acm.FP32_DEV)):
+        s = acm.Solver(acm.make_params((n, n), nu=nu, bc=[1, 1, 1, 2, 0, 0], lid_u=(lid, 0, 0),
+                                       precision=prec))
+        s.set_fields(rho, u, v)
+        steps, hist, reached = 0, [], False
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        while steps < max_steps and time.perf_counter() - t0 < max_seconds:
+            s.step(chunk)
+            steps += chunk
+            d = float(s.reduce()[5])
+            hist.append(d)
+            if d < 1e-9:
+                reached = True
+                break
+            if prec == acm.FP32_DEV and steps >= out["fp64"]["steps"]:
+                break  # as many steps as the FP64 run needed
+        secs = time.perf_counter() - t0
+        fields[name] = s.fields()
+        out[name] = {"steps": steps, "seconds": secs, "GLUPS": n * n * steps / secs / 1e9,
+                     "criterion_reached": reached, "last_max_dU": hist[-1]}
+        s.close()
+    f64, f32 = fields["fp64"], fields["fp32"]
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    out["fp32_vs_fp64"] = {"u_rel_l2": rel(f32[1], f64[1]), "v_rel_l2": rel(f32[2], f64[2])}
+    c = n // 2
+    out["centreline"] = {"u_min_vertical": float(f64[1][:, c].min()) / lid,
+                         "v_max_horizontal": float(f64[2][c, :].max()) / lid,
+                         "v_min_horizontal": float(f64[2][c, :].min()) / lid}
+    print(json.dumps({
+        "metric": "time to steady state", "value": out["fp64"]["seconds"], "unit": "s",
+        "n_gpus": 1, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "lid-driven cavity 1024^2, lid 0.1, Re=1000, from rest to "
+                               "max|d|u|| < 1e-9 per step; FP64 vs FP32 deviation storage"},
+        "runs": out}))
+    return 0
+
+
 def run_dpsl(args):
     """The paper's doubly periodic shear layer (Section 3.3: N_L = 320,
     N_t = 16000, Re = 1e4, 0 <= t <= 1) timed end to end on the GPU in FP64
@@ -631,7 +688,7 @@ def main():
     ap.add_argument("--no-fp64-check", action="store_true",
                     help="skip the FP64 accuracy run of the tgv3d bench (profiling runs)")
     ap.add_argument("--workload", default="tgv3d", choices=["tgv3d", "drops", "closure", "dpsl", "subdomains", "mames",
-                             "twophase3d"],
+                             "twophase3d", "cavity"],
                     help="tgv3d: the bench line; drops: the batched two-phase workload; "
                          "closure: the learned closure's time-to-eps comparison")
     ap.add_argument("--train-trajectories", type=int, default=32)
@@ -661,6 +718,8 @@ def main():
         return run_mames(args)
     if args.workload == "twophase3d":
         return run_twophase3d(args)
+    if args.workload == "cavity":
+        return run_cavity(args)
 
     import numpy as np
     import torch
