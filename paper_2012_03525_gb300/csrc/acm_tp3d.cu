@@ -8,8 +8,8 @@
 // beyond the wall = mirror of the node one inside, plus 2 (2/W) cos(theta)
 // (1 - phi_w^2) for phi).
 //
-// Five launches per step, one thread per node (x fastest, coalesced; the
-// 19-point neighbourhoods come through L1/L2):
+// Five launches per step, one thread per node (3D launch grid, x fastest,
+// coalesced; the 19-point neighbourhoods come through L1/L2):
 //   1. mu^n from phi^n;
 //   2. Delta rho = rho^{n+1} - rho^n (Eq. 2.10; wall nodes take the
 //      second-order zero-normal-gradient extrapolation of rho^{n+1});
@@ -20,8 +20,6 @@
 // with R(f, m) = -u^n . grad f + M Lap m.  Scratch fields: mu, phi*,
 // Delta rho.  Storage is the padded 3D layout of the single-phase step
 // (periodic images are not needed: every index wraps explicitly).
-#include <algorithm>
-
 #include "acm_internal.h"
 
 namespace acm {
@@ -29,11 +27,16 @@ namespace {
 
 constexpr int TPB = 256;
 
-// D3Q19 velocities without the rest one: 6 axis, 12 edges
-__constant__ int8_t c_vel[18][3] = {
-    {1, 0, 0},  {-1, 0, 0}, {0, 1, 0},  {0, -1, 0}, {0, 0, 1},   {0, 0, -1},
-    {1, 1, 0},  {1, -1, 0}, {-1, 1, 0}, {-1, -1, 0}, {1, 0, 1},  {1, 0, -1},
-    {-1, 0, 1}, {-1, 0, -1}, {0, 1, 1}, {0, 1, -1},  {0, -1, 1}, {0, -1, -1}};
+// D3Q19 velocities without the rest one: 6 axis, 12 edges.  A compile-time
+// table: in the unrolled loops below every offset folds to a constant.
+__host__ __device__ constexpr int vel(int i, int d)
+{
+    constexpr int8_t t[18][3] = {
+        {1, 0, 0},  {-1, 0, 0}, {0, 1, 0},  {0, -1, 0}, {0, 0, 1},   {0, 0, -1},
+        {1, 1, 0},  {1, -1, 0}, {-1, 1, 0}, {-1, -1, 0}, {1, 0, 1},  {1, 0, -1},
+        {-1, 0, 1}, {-1, 0, -1}, {0, 1, 1}, {0, 1, -1},  {0, -1, 1}, {0, -1, -1}};
+    return t[i][d];
+}
 
 struct Geo3 {
     int nx, ny, nz;
@@ -57,33 +60,63 @@ struct Geo3 {
 
 enum { K_MIRROR = 0, K_WET = 1 };
 
-// field value at (x, y, z) where z may lie one node beyond a wall face
-template <typename T, int KIND>
-__device__ __forceinline__ T val(const T *f, const Geo3 &g, int x, int y, int z, T wet)
-{
-    if (g.zwall && (z < 0 || z >= g.nz)) {
-        const int zm = z < 0 ? 1 : g.nz - 2, zw = z < 0 ? 0 : g.nz - 1;
-        T v = f[g.at(x, y, zm)];
-        if (KIND == K_WET) {
-            const T fw = f[g.at(x, y, zw)];
-            v += wet * (T(1) - fw * fw);
+// Storage offsets of a node's 3 x 3 x 3 neighbourhood: x and y wrap; z wraps
+// when periodic, and beyond a wall face points at the mirror plane (ghost
+// node = node one inside the wall), with the wall plane kept for the
+// wetting term.
+struct Hood {
+    long long xo[3], yo[3], zo[3], zw[3];
+    bool ghost[3];
+    __device__ __forceinline__ Hood(const Geo3 &g, int x, int y, int z)
+    {
+        xo[0] = g.wx(x - 1);
+        xo[1] = x;
+        xo[2] = g.wx(x + 1);
+        yo[0] = (long long)g.wy(y - 1) * g.px;
+        yo[1] = (long long)y * g.px;
+        yo[2] = (long long)g.wy(y + 1) * g.px;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            int zz = z + k - 1, wall = zz;
+            ghost[k] = false;
+            if (g.zwall) {
+                if (zz < 0) {
+                    zz = 1;
+                    wall = 0;
+                    ghost[k] = true;
+                } else if (zz >= g.nz) {
+                    zz = g.nz - 2;
+                    wall = g.nz - 1;
+                    ghost[k] = true;
+                }
+            } else {
+                zz = g.wz(zz);
+                wall = zz;
+            }
+            zo[k] = g.base + (long long)zz * g.pxy;
+            zw[k] = g.base + (long long)wall * g.pxy;
         }
-        return v;
     }
-    return f[g.at(x, y, z)];
-}
+};
 
 // D3Q19 isotropic Laplacian (2/c_s^2) sum w_i (f_i - f_0) and gradient
-// (1/c_s^2) sum w_i e_i f_i at a node
+// (1/c_s^2) sum w_i e_i f_i at a node; ghost nodes beyond a wall take the
+// mirror value, plus (KIND == K_WET) the wetting term wet (1 - f_w^2) with
+// f_w the wall node below/above them
 template <typename T, int KIND>
-__device__ __forceinline__ void iso_ops(const T *f, const Geo3 &g, int x, int y, int z, T wet,
-                                        T f0, T &lap, T &gx, T &gy, T &gz)
+__device__ __forceinline__ void iso_ops(const T *f, const Hood &h, T wet, T f0, T &lap, T &gx,
+                                        T &gy, T &gz)
 {
     T la = T(0), le = T(0), ax = T(0), ay = T(0), az = T(0), ex = T(0), ey = T(0), ez = T(0);
 #pragma unroll
     for (int i = 0; i < 18; ++i) {
-        const int dx = c_vel[i][0], dy = c_vel[i][1], dz = c_vel[i][2];
-        const T fi = val<T, KIND>(f, g, x + dx, y + dy, z + dz, wet);
+        const int dx = vel(i, 0), dy = vel(i, 1), dz = vel(i, 2);
+        const long long xy = h.yo[dy + 1] + h.xo[dx + 1];
+        T fi = f[h.zo[dz + 1] + xy];
+        if (KIND == K_WET && dz != 0 && h.ghost[dz + 1]) {
+            const T fw = f[h.zw[dz + 1] + xy];
+            fi += wet * (T(1) - fw * fw);
+        }
         if (i < 6) {
             la += fi - f0;
             ax += dx * fi;
@@ -102,15 +135,6 @@ __device__ __forceinline__ void iso_ops(const T *f, const Geo3 &g, int x, int y,
     gz = T(1.0 / 6.0) * az + T(1.0 / 12.0) * ez;
 }
 
-__device__ __forceinline__ void node_of(long long i, int nx, int ny, int &x, int &y, int &z)
-{
-    const long long nxy = (long long)nx * ny;
-    z = (int)(i / nxy);
-    const long long r = i - (long long)z * nxy;
-    y = (int)(r / nx);
-    x = (int)(r - (long long)y * nx);
-}
-
 // 1, 4: mu = 4 a phi (phi^2 - 1) - kappa Lap_iso(phi)
 template <typename T>
 __global__ void __launch_bounds__(TPB) k_mu(const RunDesc R, const T *__restrict__ phi,
@@ -119,17 +143,17 @@ __global__ void __launch_bounds__(TPB) k_mu(const RunDesc R, const T *__restrict
     const Geo3 g(R);
     const T *C = coefs<T>(R);
     const T a = C[C_A], kappa = C[C_KAPPA], wet = C[C_WET];
-    const long long n = (long long)g.nx * g.ny * g.nz;
-    for (long long i = (long long)blockIdx.x * TPB + threadIdx.x; i < n;
-         i += (long long)gridDim.x * TPB) {
-        int x, y, z;
-        node_of(i, g.nx, g.ny, x, y, z);
-        const long long c = g.at(x, y, z);
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z * blockDim.z + threadIdx.z;
+    if (x < g.nx && y < g.ny && z < g.nz) do {  // one node per thread
+        const Hood h(g, x, y, z);
+        const long long c = h.zo[1] + h.yo[1] + h.xo[1];
         const T f = phi[c];
         T lap, gx, gy, gz;
-        iso_ops<T, K_WET>(phi, g, x, y, z, wet, f, lap, gx, gy, gz);
+        iso_ops<T, K_WET>(phi, h, wet, f, lap, gx, gy, gz);
         mu[c] = T(4) * a * f * (f * f - T(1)) - kappa * lap;
-    }
+    } while (0);
 }
 
 // Eq. (2.10) at a non-wall node: Delta rho = -dt div(rho u) + satc Lap(rho')
@@ -156,11 +180,10 @@ __global__ void __launch_bounds__(TPB) k_drho(const RunDesc R, Fields<T> in, T *
     const Geo3 g(R);
     const T *C = coefs<T>(R);
     const T rho0 = C[C_RHO0], dt = C[C_DT], satc = C[C_SATC];
-    const long long n = (long long)g.nx * g.ny * g.nz;
-    for (long long i = (long long)blockIdx.x * TPB + threadIdx.x; i < n;
-         i += (long long)gridDim.x * TPB) {
-        int x, y, z;
-        node_of(i, g.nx, g.ny, x, y, z);
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z * blockDim.z + threadIdx.z;
+    if (x < g.nx && y < g.ny && z < g.nz) do {  // one node per thread
         const long long c = g.at(x, y, z);
         if (!g.wall(z)) {
             dr[c] = drho_at(in, g, x, y, z, rho0, dt, satc);
@@ -171,7 +194,7 @@ __global__ void __launch_bounds__(TPB) k_drho(const RunDesc R, Fields<T> in, T *
         const T r1 = r[g.at(x, y, z + s)] + drho_at(in, g, x, y, z + s, rho0, dt, satc);
         const T r2 = r[g.at(x, y, z + 2 * s)] + drho_at(in, g, x, y, z + 2 * s, rho0, dt, satc);
         dr[c] = (T(4) * r1 - r2) / T(3) - r[c];
-    }
+    } while (0);
 }
 
 // 3: rho^{n+1}, u^{n+1} and phi*
@@ -186,23 +209,24 @@ __global__ void __launch_bounds__(TPB)
     const T satm = C[C_SATM], mob = C[C_M], wet = C[C_WET];
     const T gfx = C[C_GX], gfy = C[C_GY], gfz = C[C_GZ];
     const T *r = in.f[F_R], *u = in.f[F_U], *v = in.f[F_V], *w = in.f[F_W], *ph = in.f[F_PHI];
-    const long long n = (long long)g.nx * g.ny * g.nz;
     bool bad = false;
-    for (long long i = (long long)blockIdx.x * TPB + threadIdx.x; i < n;
-         i += (long long)gridDim.x * TPB) {
-        int x, y, z;
-        node_of(i, g.nx, g.ny, x, y, z);
-        const long long c = g.at(x, y, z);
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z * blockDim.z + threadIdx.z;
+    if (x < g.nx && y < g.ny && z < g.nz) do {  // one node per thread
+        const Hood h(g, x, y, z);
+        const long long c = h.zo[1] + h.yo[1] + h.xo[1];
         const T r0 = r[c], d0 = dr[c];
         const T rho1 = rho0 + r0 + d0;
         const T u0 = u[c], v0 = v[c], w0 = w[c], f0 = ph[c];
         // mu^n: Laplacian for the CHE and gradient for F_ST
         T lmu, gmx, gmy, gmz;
-        iso_ops<T, K_MIRROR>(mu, g, x, y, z, T(0), mu[c], lmu, gmx, gmy, gmz);
+        iso_ops<T, K_MIRROR>(mu, h, T(0), mu[c], lmu, gmx, gmy, gmz);
         T un = T(0), vn = T(0), wn = T(0);
         if (!g.wall(z)) {
-            const long long nb[6] = {g.at(x + 1, y, z), g.at(x - 1, y, z), g.at(x, y + 1, z),
-                                     g.at(x, y - 1, z), g.at(x, y, z + 1), g.at(x, y, z - 1)};
+            const long long nb[6] = {h.zo[1] + h.yo[1] + h.xo[2], h.zo[1] + h.yo[1] + h.xo[0],
+                                     h.zo[1] + h.yo[2] + h.xo[1], h.zo[1] + h.yo[0] + h.xo[1],
+                                     h.zo[2] + h.yo[1] + h.xo[1], h.zo[0] + h.yo[1] + h.xo[1]};
             T q[6], mx[6], my[6], mz[6];
 #pragma unroll
             for (int k = 0; k < 6; ++k) {
@@ -238,7 +262,7 @@ __global__ void __launch_bounds__(TPB)
         }
         // first Heun stage of Eq. (2.14), u^n frozen
         T lph, gpx, gpy, gpz;
-        iso_ops<T, K_WET>(ph, g, x, y, z, wet, f0, lph, gpx, gpy, gpz);
+        iso_ops<T, K_WET>(ph, h, wet, f0, lph, gpx, gpy, gpz);
         const T fs = f0 + dt * (-(u0 * gpx + v0 * gpy + w0 * gpz) + mob * lmu);
         const T rn = r0 + d0;
         out.f[F_R][c] = rn;
@@ -247,7 +271,7 @@ __global__ void __launch_bounds__(TPB)
         out.f[F_W][c] = wn;
         phs[c] = fs;
         bad |= !isfinite(rn + un + vn + wn + fs);
-    }
+    } while (0);
     if (bad) atomicOr(err, ERR_NONFINITE);
 }
 
@@ -261,21 +285,21 @@ __global__ void __launch_bounds__(TPB)
     const T *C = coefs<T>(R);
     const T dt = C[C_DT], mob = C[C_M], wet = C[C_WET];
     const T *u = in.f[F_U], *v = in.f[F_V], *w = in.f[F_W], *ph = in.f[F_PHI];
-    const long long n = (long long)g.nx * g.ny * g.nz;
     bool bad = false;
-    for (long long i = (long long)blockIdx.x * TPB + threadIdx.x; i < n;
-         i += (long long)gridDim.x * TPB) {
-        int x, y, z;
-        node_of(i, g.nx, g.ny, x, y, z);
-        const long long c = g.at(x, y, z);
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z * blockDim.z + threadIdx.z;
+    if (x < g.nx && y < g.ny && z < g.nz) do {  // one node per thread
+        const Hood h(g, x, y, z);
+        const long long c = h.zo[1] + h.yo[1] + h.xo[1];
         T lmu, a0, a1, a2, lph, gpx, gpy, gpz;
-        iso_ops<T, K_MIRROR>(mus, g, x, y, z, T(0), mus[c], lmu, a0, a1, a2);
-        iso_ops<T, K_WET>(phs, g, x, y, z, wet, phs[c], lph, gpx, gpy, gpz);
+        iso_ops<T, K_MIRROR>(mus, h, T(0), mus[c], lmu, a0, a1, a2);
+        iso_ops<T, K_WET>(phs, h, wet, phs[c], lph, gpx, gpy, gpz);
         const T r2 = -(u[c] * gpx + v[c] * gpy + w[c] * gpz) + mob * lmu;
         const T f = T(0.5) * (ph[c] + phs[c] + dt * r2);
         phn[c] = f;
         bad |= !isfinite(f);
-    }
+    } while (0);
     if (bad) atomicOr(err, ERR_NONFINITE);
 }
 
@@ -285,13 +309,15 @@ template <typename T>
 cudaError_t launch_tp3d(const RunDesc &R, Fields<T> in, Fields<T> out, T *mu, T *phs, T *dr,
                         unsigned *err, int sms, cudaStream_t s)
 {
-    const long long n = (long long)R.nx * R.ny * R.nz;
-    const int blocks = (int)std::min<long long>((n + TPB - 1) / TPB, 8LL * sms);
-    k_mu<T><<<blocks, TPB, 0, s>>>(R, in.f[F_PHI], mu);
-    k_drho<T><<<blocks, TPB, 0, s>>>(R, in, dr);
-    k_main<T><<<blocks, TPB, 0, s>>>(R, in, out, dr, mu, phs, err);
-    k_mu<T><<<blocks, TPB, 0, s>>>(R, phs, mu);
-    k_phi<T><<<blocks, TPB, 0, s>>>(R, in, phs, mu, out.f[F_PHI], err);
+    (void)sms;
+    // one thread per node: 32 x 4 x 2 blocks (x fastest, coalesced rows)
+    const dim3 blk(32, 4, 2);
+    const dim3 grid((R.nx + 31) / 32, (R.ny + 3) / 4, (R.nz + 1) / 2);
+    k_mu<T><<<grid, blk, 0, s>>>(R, in.f[F_PHI], mu);
+    k_drho<T><<<grid, blk, 0, s>>>(R, in, dr);
+    k_main<T><<<grid, blk, 0, s>>>(R, in, out, dr, mu, phs, err);
+    k_mu<T><<<grid, blk, 0, s>>>(R, phs, mu);
+    k_phi<T><<<grid, blk, 0, s>>>(R, in, phs, mu, out.f[F_PHI], err);
     return cudaGetLastError();
 }
 
