@@ -6,7 +6,9 @@
 // Work decomposition: a persistent grid of CTAs walks a list of
 // (run, tile_x0, tile_y0) items.  Each item is a T2X x T2Y tile of outputs.
 // The CTA stages the tile plus its halo (radius 2 for rho', u, v; radius 4
-// for phi) in shared memory, then computes, all on chip:
+// for phi) in shared memory -- asynchronously (cp.async) into one of two
+// staging sets, the next item's copies in flight while the current item is
+// computed -- then computes, all on chip:
 //   1. Delta rho = rho^{n+1} - rho^n on the tile grown by one node (Eq. 2.10),
 //      so that d_a rho^{n+1} - d_a rho^n of Eq. (2.11) is a centred
 //      difference of Delta rho; wall nodes take the second-order
@@ -137,6 +139,26 @@ __device__ __forceinline__ void wall_ghosts(T *f, int x0, int y0, int nx, int ny
     }
 }
 
+// asynchronous global -> shared copy of one element (cp.async, bypasses the
+// registers), grouped per work item so the next item's staging overlaps
+// the current item's compute
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T *dst, const T *src)
+{
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(src), "n"(sizeof(T))
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit()
+{
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 template <typename T>
 __device__ __forceinline__ bool bad(T x)
 {
@@ -149,18 +171,54 @@ __global__ void __launch_bounds__(T2THREADS)
              Fields<T> in, Fields<T> out, unsigned *err)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *sr = reinterpret_cast<T *>(smem_raw);
-    T *su = sr + A2;
-    T *sv = su + A2;
-    T *sdr = sv + A2;
-    T *sphi = sdr + A1;   // two-phase only from here on
-    T *smu = sphi + A4;
+    // two staging sets (rho', u, v with halo 2; phi with halo 4): the next
+    // work item is copied in while the current one is computed
+    constexpr int STAGE = 3 * A2 + (TP ? A4 : 0);
+    T *stage0 = reinterpret_cast<T *>(smem_raw);
+    T *sdr = stage0 + 2 * STAGE;
+    T *smu = sdr + A1;    // two-phase only from here on
     T *sphs = smu + A3;
     T *smus = sphs + A2;
     const int tid = threadIdx.x, lane = tid & 31;
     bool nonfinite = false;
 
-    for (int item = blockIdx.x; item < nwork; item += gridDim.x) {
+    // issue the asynchronous copies of work item `it` into staging set `b`
+    auto stage = [&](int it, int b) {
+        const int4 wk = work[it];
+        const RunDesc &R = runs[wk.x];
+        const int nx = R.nx, ny = R.ny;
+        const int x0 = wk.y, y0 = wk.z;
+        const bool perx = R.bc[0] == ACM_BC_PERIODIC;
+        const bool pery = R.bc[2] == ACM_BC_PERIODIC;
+        const long long off = R.off;
+        const T *gr = in.f[F_R] + off, *gu = in.f[F_U] + off, *gv = in.f[F_V] + off;
+        T *dr_ = stage0 + b * STAGE, *du = dr_ + A2, *dv = du + A2, *dp = dv + A2;
+        // window columns of this lane (halo 2: rho', u, v; halo 4: phi)
+        const int c2a = wrap_or_clamp(x0 - 2 + lane, nx, perx);
+        const int c2b = wrap_or_clamp(x0 - 2 + lane + 32, nx, perx);
+        for_window<RW2, RH2>([&](int ly, int lx) {
+            const long long row = (long long)wrap_or_clamp(y0 - 2 + ly, ny, pery) * nx;
+            const long long k = row + (lx < 32 ? c2a : c2b);
+            const int i = ly * RW2 + lx;
+            cp_async_elem(dr_ + i, gr + k);
+            cp_async_elem(du + i, gu + k);
+            cp_async_elem(dv + i, gv + k);
+        });
+        if (TP) {
+            const T *gp = in.f[F_PHI] + off;
+            const int c4a = wrap_or_clamp(x0 - 4 + lane, nx, perx);
+            const int c4b = wrap_or_clamp(x0 - 4 + lane + 32, nx, perx);
+            for_window<RW4, RH4>([&](int ly, int lx) {
+                const long long row = (long long)wrap_or_clamp(y0 - 4 + ly, ny, pery) * nx;
+                cp_async_elem(dp + ly * RW4 + lx, gp + row + (lx < 32 ? c4a : c4b));
+            });
+        }
+    };
+
+    if ((int)blockIdx.x < nwork) stage(blockIdx.x, 0);
+    cp_async_commit();
+    int buf = 0;
+    for (int item = blockIdx.x; item < nwork; item += gridDim.x, buf ^= 1) {
         const int4 wk = work[item];
         const RunDesc &R = runs[wk.x];
         const int nx = R.nx, ny = R.ny;
@@ -171,31 +229,12 @@ __global__ void __launch_bounds__(T2THREADS)
         const T rho0 = C[C_RHO0], dt = C[C_DT], nudt = C[C_NUDT], satc = C[C_SATC];
         const T cs2 = C[C_CS2];
         const long long off = R.off;
-        const T *gr = in.f[F_R] + off, *gu = in.f[F_U] + off, *gv = in.f[F_V] + off;
+        T *sr = stage0 + buf * STAGE, *su = sr + A2, *sv = su + A2, *sphi = sv + A2;
 
-        __syncthreads();  // shared memory of the previous item is free
-        {
-            // window columns of this lane (halo 2: rho', u, v; halo 4: phi)
-            const int c2a = wrap_or_clamp(x0 - 2 + lane, nx, perx);
-            const int c2b = wrap_or_clamp(x0 - 2 + lane + 32, nx, perx);
-            for_window<RW2, RH2>([&](int ly, int lx) {
-                const long long row = (long long)wrap_or_clamp(y0 - 2 + ly, ny, pery) * nx;
-                const long long k = row + (lx < 32 ? c2a : c2b);
-                const int i = ly * RW2 + lx;
-                sr[i] = gr[k];
-                su[i] = gu[k];
-                sv[i] = gv[k];
-            });
-            if (TP) {
-                const T *gp = in.f[F_PHI] + off;
-                const int c4a = wrap_or_clamp(x0 - 4 + lane, nx, perx);
-                const int c4b = wrap_or_clamp(x0 - 4 + lane + 32, nx, perx);
-                for_window<RW4, RH4>([&](int ly, int lx) {
-                    const long long row = (long long)wrap_or_clamp(y0 - 4 + ly, ny, pery) * nx;
-                    sphi[ly * RW4 + lx] = gp[row + (lx < 32 ? c4a : c4b)];
-                });
-            }
-        }
+        __syncthreads();  // the previous item no longer reads shared memory
+        if (item + (int)gridDim.x < nwork) stage(item + gridDim.x, buf ^ 1);
+        cp_async_commit();
+        cp_async_wait<1>();  // this item's copies (issued one item earlier) have landed
         __syncthreads();
 
         const T a = C[C_A], kappa = C[C_KAPPA], mob = C[C_M];
@@ -345,14 +384,15 @@ __global__ void __launch_bounds__(T2THREADS)
             nonfinite |= bad(chk);
         });
     }
+    cp_async_wait<0>();  // no copy left in flight at exit
     if (nonfinite) atomicOr(err, ERR_NONFINITE);
 }
 
 template <typename T, bool TP>
 size_t smem_bytes()
 {
-    size_t n = 3 * A2 + A1;
-    if (TP) n += A4 + A3 + A2 + A1;
+    size_t n = 2 * (3 * A2 + (TP ? A4 : 0)) + A1;
+    if (TP) n += A3 + A2 + A1;
     return n * sizeof(T);
 }
 
