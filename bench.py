@@ -789,15 +789,27 @@ def main():
     accuracy = None
     if not args.no_fp64_check:
         ref = acm.Solver(acm.make_params((n3, n3, n3), nu=nu, precision=acm.FP64))
+        ref.set_stream(stream.cuda_stream)
         ref.set_fields(rho, u, v, w)
+        ref.step(64)
+        ref.sync()
+        ref.set_fields(rho, u, v, w)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
         ref.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
         f64 = ref.fields()[:4]
         ref.close()
         f32 = [o.numpy() for o in outs]
         rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
         accuracy = {"steps": args.steps,
                     "u_rel_l2_vs_fp64": max(rel(f32[k], f64[k]) for k in (1, 2, 3)),
-                    "rho_dev_rel_l2_vs_fp64": rel(f32[0] - 1.0, f64[0] - 1.0)}
+                    "rho_dev_rel_l2_vs_fp64": rel(f32[0] - 1.0, f64[0] - 1.0),
+                    "fp64_GLUPS": nodes * args.steps / (ms64 / 1e3) / 1e9,
+                    "fp32_speedup_over_fp64": ms64 / ms}
 
     glups = multirank.job_throughput(nodes, args.steps, world, ms / 1e3)
     per_launch_s = ms / 1e3 / args.steps
@@ -818,6 +830,7 @@ def main():
                    "graph_steps": 64},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": f"{peak_kind} copy bandwidth",
+                     "frac_of_nominal_8tbs": achieved / 8000.0,
                      "traffic": profiled_traffic(),
                      "algorithmic_bytes_per_launch": BYTES_PER_LU_FP32 * nodes},
         "e2e": {"value": multirank.job_throughput(nodes, args.steps, world, e2e_s), "unit": "GLUPS",
