@@ -10,9 +10,20 @@
 #include <cstring>
 #include <new>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "acm_internal.h"
 
 using namespace acm;
+
+namespace {
+// NVTX range over one API call (visible in Nsight timelines; no cost when no
+// tool is attached)
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+}  // namespace
 
 struct acm_handle {
     int nruns = 0, dim = 2, prec = ACM_FP64, two_phase = 0, any_wall = 0;
@@ -679,6 +690,7 @@ int acm_get_tuning(const acm_handle *h, int key)
 
 acm_status acm_autotune(acm_handle *h, int nsteps, double *best_ms_per_step)
 {
+    NvtxRange nvtx_("acm_autotune");
     if (!h) return fail(nullptr, ACM_EINVAL, "null handle");
     if (nsteps < 1) return fail(h, ACM_EINVAL, "nsteps must be >= 1");
     for (int r = 0; r < h->nruns; ++r)
@@ -795,6 +807,7 @@ acm_status acm_autotune(acm_handle *h, int nsteps, double *best_ms_per_step)
 acm_status acm_set_fields(acm_handle *h, int run, const double *rho, const double *u,
                           const double *v, const double *w, const double *phi)
 {
+    NvtxRange nvtx_("acm_set_fields");
     if (!h) return fail(nullptr, ACM_EINVAL, "null handle");
     if (run < 0 || run >= h->nruns) return fail(h, ACM_EINVAL, "run index out of range");
     if (!rho || !u || !v || (h->dim == 3 && !w) || (h->two_phase && !phi))
@@ -827,6 +840,7 @@ acm_status acm_set_fields(acm_handle *h, int run, const double *rho, const doubl
 
 acm_status acm_step(acm_handle *h, int64_t nsteps)
 {
+    NvtxRange nvtx_("acm_step");
     if (!h) return fail(nullptr, ACM_EINVAL, "null handle");
     if (nsteps < 0) return fail(h, ACM_EINVAL, "nsteps must be >= 0");
     for (int r = 0; r < h->nruns; ++r)
@@ -860,6 +874,7 @@ acm_status acm_step(acm_handle *h, int64_t nsteps)
 
 acm_status acm_sync(acm_handle *h)
 {
+    NvtxRange nvtx_("acm_sync");
     if (!h) return fail(nullptr, ACM_EINVAL, "null handle");
     CK(h, cudaSetDevice(h->device));
     return check_flags(h);
@@ -868,6 +883,7 @@ acm_status acm_sync(acm_handle *h)
 acm_status acm_fields(acm_handle *h, int run, double *rho, double *u, double *v, double *w,
                       double *phi)
 {
+    NvtxRange nvtx_("acm_fields");
     if (!h) return fail(nullptr, ACM_EINVAL, "null handle");
     if (run < 0 || run >= h->nruns) return fail(h, ACM_EINVAL, "run index out of range");
     CK(h, cudaSetDevice(h->device));
@@ -892,6 +908,7 @@ acm_status acm_fields(acm_handle *h, int run, double *rho, double *u, double *v,
 
 acm_status acm_reduce_mass(acm_handle *h, double *out)
 {
+    NvtxRange nvtx_("acm_reduce_mass");
     if (!h || !out) return fail(h, ACM_EINVAL, "null argument");
     CK(h, cudaSetDevice(h->device));
     const int prev = 1 - h->cur;
