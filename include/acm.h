@@ -227,7 +227,8 @@ acm_status acm_restrict(acm_handle *fine, acm_handle *coarse, int factor, double
  * (rho' s_rho, u s_u, v s_u).  BF16 weights and activations on the tensor
  * cores, FP32 accumulation, FP32 master weights trained with Adam.  This is
  * an addition to the method of the paper (a learned correction of the coarse
- * scheme); the scheme itself stays the judge of its error.
+ * scheme); the plain scheme remains the reference its error is measured
+ * against.
  *
  * Normalised state tensors are FP32 [batch][3][ny][nx] in device memory
  * (channel 0 = s_rho rho', 1 = s_u u, 2 = s_u v).  Weights are a flat FP32
