@@ -60,63 +60,89 @@ struct Geo3 {
 
 enum { K_MIRROR = 0, K_WET = 1 };
 
-// Storage offsets of a node's 3 x 3 x 3 neighbourhood: x and y wrap; z wraps
-// when periodic, and beyond a wall face points at the mirror plane (ghost
-// node = node one inside the wall), with the wall plane kept for the
-// wetting term.
-struct Hood {
-    long long xo[3], yo[3], zo[3], zw[3];
-    bool ghost[3];
-    __device__ __forceinline__ Hood(const Geo3 &g, int x, int y, int z)
+// z-marching tiles for the D3Q19 operators: a CTA of BX x BY threads owns a
+// BX x BY column of the x-y plane and walks ZCH planes up it, keeping the
+// planes z-1, z, z+1 of each operand field in shared memory as windows with
+// a one-node halo (ghost planes beyond a wall included), so a node's 18
+// neighbours are shared-memory reads and each value comes from memory about
+// once per plane instead of once per neighbour.
+#ifndef ACM_TP3D_ZCH
+#define ACM_TP3D_ZCH 8
+#endif
+constexpr int BX = 32, BY = 8, ZCH = ACM_TP3D_ZCH;
+constexpr int WX = BX + 2, WY = BY + 2, WP = WX * WY;
+
+// index c in [-1, n + BX] wrapped into [0, n) (a full modulo only for grids
+// narrower than a tile)
+__device__ __forceinline__ int wrapc(int c, int n)
+{
+    if (c < 0) c += n;
+    else if (c >= n) c -= n;
+    if ((unsigned)c >= (unsigned)n) {
+        c %= n;
+        if (c < 0) c += n;
+    }
+    return c;
+}
+
+// storage offsets of a node and its six axis neighbours (x, y wrap; z wraps
+// when periodic; at a wall node the z neighbours beyond it are not used)
+struct Axis7 {
+    long long c, xe, xw, yn, ys, zu, zd;
+    __device__ __forceinline__ Axis7(const Geo3 &g, int x, int y, int z)
     {
-        xo[0] = g.wx(x - 1);
-        xo[1] = x;
-        xo[2] = g.wx(x + 1);
-        yo[0] = (long long)g.wy(y - 1) * g.px;
-        yo[1] = (long long)y * g.px;
-        yo[2] = (long long)g.wy(y + 1) * g.px;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            int zz = z + k - 1, wall = zz;
-            ghost[k] = false;
-            if (g.zwall) {
-                if (zz < 0) {
-                    zz = 1;
-                    wall = 0;
-                    ghost[k] = true;
-                } else if (zz >= g.nz) {
-                    zz = g.nz - 2;
-                    wall = g.nz - 1;
-                    ghost[k] = true;
-                }
-            } else {
-                zz = g.wz(zz);
-                wall = zz;
-            }
-            zo[k] = g.base + (long long)zz * g.pxy;
-            zw[k] = g.base + (long long)wall * g.pxy;
-        }
+        c = g.base + (long long)z * g.pxy + (long long)y * g.px + x;
+        xe = c + (x == g.nx - 1 ? 1 - g.nx : 1);
+        xw = c - (x == 0 ? 1 - g.nx : 1);
+        yn = c + (y == g.ny - 1 ? (1 - g.ny) * g.px : g.px);
+        ys = c - (y == 0 ? (1 - g.ny) * g.px : g.px);
+        const bool zp = !g.zwall;
+        zu = c + (zp && z == g.nz - 1 ? (1 - g.nz) * g.pxy : g.pxy);
+        zd = c - (zp && z == 0 ? (1 - g.nz) * g.pxy : g.pxy);
     }
 };
 
-// D3Q19 isotropic Laplacian (2/c_s^2) sum w_i (f_i - f_0) and gradient
-// (1/c_s^2) sum w_i e_i f_i at a node; ghost nodes beyond a wall take the
-// mirror value, plus (KIND == K_WET) the wetting term wet (1 - f_w^2) with
-// f_w the wall node below/above them
+// window of plane z (z in [-1, nz]) of field f around the tile at (x0, y0):
+// x and y wrap; beyond a wall face the mirror plane, plus (KIND == K_WET)
+// the wetting term wet (1 - f_w^2) of the wall plane
 template <typename T, int KIND>
-__device__ __forceinline__ void iso_ops(const T *f, const Hood &h, T wet, T f0, T &lap, T &gx,
-                                        T &gy, T &gz)
+__device__ __forceinline__ void load_window(T *dst, const T *__restrict__ f, const Geo3 &g,
+                                            int x0, int y0, int z, T wet)
 {
+    const int tid = threadIdx.y * BX + threadIdx.x;
+    for (int i = tid; i < WP; i += BX * BY) {
+        const int wy = i / WX, wx = i - wy * WX;
+        const int xx = wrapc(x0 - 1 + wx, g.nx), yy = wrapc(y0 - 1 + wy, g.ny);
+        const long long xy = g.base + (long long)yy * g.px + xx;
+        T val;
+        if (g.zwall && (z < 0 || z >= g.nz)) {
+            const int zm = z < 0 ? 1 : g.nz - 2, zw = z < 0 ? 0 : g.nz - 1;
+            val = f[xy + (long long)zm * g.pxy];
+            if (KIND == K_WET) {
+                const T fw = f[xy + (long long)zw * g.pxy];
+                val += wet * (T(1) - fw * fw);
+            }
+        } else {
+            val = f[xy + (long long)(g.zwall ? z : g.wz(z)) * g.pxy];
+        }
+        dst[i] = val;
+    }
+}
+
+// D3Q19 isotropic Laplacian (2/c_s^2) sum w_i (f_i - f_0) and gradient
+// (1/c_s^2) sum w_i e_i f_i at window position c, planes z-1, z, z+1 in
+// wm, w0, wp
+template <typename T>
+__device__ __forceinline__ void iso_ops(const T *wm, const T *w0, const T *wp, int c, T &lap,
+                                        T &gx, T &gy, T &gz)
+{
+    const T f0 = w0[c];
     T la = T(0), le = T(0), ax = T(0), ay = T(0), az = T(0), ex = T(0), ey = T(0), ez = T(0);
 #pragma unroll
     for (int i = 0; i < 18; ++i) {
         const int dx = vel(i, 0), dy = vel(i, 1), dz = vel(i, 2);
-        const long long xy = h.yo[dy + 1] + h.xo[dx + 1];
-        T fi = f[h.zo[dz + 1] + xy];
-        if (KIND == K_WET && dz != 0 && h.ghost[dz + 1]) {
-            const T fw = f[h.zw[dz + 1] + xy];
-            fi += wet * (T(1) - fw * fw);
-        }
+        const T *pl = dz < 0 ? wm : (dz > 0 ? wp : w0);
+        const T fi = pl[c + dy * WX + dx];
         if (i < 6) {
             la += fi - f0;
             ax += dx * fi;
@@ -135,25 +161,45 @@ __device__ __forceinline__ void iso_ops(const T *f, const Hood &h, T wet, T f0, 
     gz = T(1.0 / 6.0) * az + T(1.0 / 12.0) * ez;
 }
 
+// Walk the CTA's z-chunk: `load(slot, z)` fills the windows of plane z,
+// `body(z, sm, s0, sp)` computes plane z from the slots of z-1, z, z+1
+template <typename L, typename B>
+__device__ __forceinline__ void zmarch(int nz, L load, B body)
+{
+    const int z0 = blockIdx.z * ZCH, zend = min(z0 + ZCH, nz);
+    load(0, z0 - 1);
+    load(1, z0);
+    for (int z = z0; z < zend; ++z) {
+        const int k = z - z0;
+        load((k + 2) % 3, z + 1);
+        __syncthreads();
+        body(z, k % 3, (k + 1) % 3, (k + 2) % 3);
+        __syncthreads();  // slot k % 3 is refilled next
+    }
+}
+
 // 1, 4: mu = 4 a phi (phi^2 - 1) - kappa Lap_iso(phi)
 template <typename T>
-__global__ void __launch_bounds__(TPB) k_mu(const RunDesc R, const T *__restrict__ phi,
-                                            T *__restrict__ mu)
+__global__ void __launch_bounds__(BX *BY) k_mu(const RunDesc R, const T *__restrict__ phi,
+                                               T *__restrict__ mu)
 {
+    __shared__ T win[3][WP];
     const Geo3 g(R);
     const T *C = coefs<T>(R);
     const T a = C[C_A], kappa = C[C_KAPPA], wet = C[C_WET];
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z * blockDim.z + threadIdx.z;
-    if (x < g.nx && y < g.ny && z < g.nz) do {  // one node per thread
-        const Hood h(g, x, y, z);
-        const long long c = h.zo[1] + h.yo[1] + h.xo[1];
-        const T f = phi[c];
-        T lap, gx, gy, gz;
-        iso_ops<T, K_WET>(phi, h, wet, f, lap, gx, gy, gz);
-        mu[c] = T(4) * a * f * (f * f - T(1)) - kappa * lap;
-    } while (0);
+    const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    const int c = (threadIdx.y + 1) * WX + threadIdx.x + 1;
+    zmarch(
+        g.nz, [&](int sl, int z) { load_window<T, K_WET>(win[sl], phi, g, x0, y0, z, wet); },
+        [&](int z, int sm, int s0, int sp) {
+            if (x >= g.nx || y >= g.ny) return;
+            T lap, gx, gy, gz;
+            iso_ops(win[sm], win[s0], win[sp], c, lap, gx, gy, gz);
+            const T f = win[s0][c];
+            mu[g.base + (long long)z * g.pxy + (long long)y * g.px + x] =
+                T(4) * a * f * (f * f - T(1)) - kappa * lap;
+        });
 }
 
 // Eq. (2.10) at a non-wall node: Delta rho = -dt div(rho u) + satc Lap(rho')
@@ -162,14 +208,11 @@ __device__ __forceinline__ T drho_at(const Fields<T> &in, const Geo3 &g, int x, 
                                      T rho0, T dt, T satc)
 {
     const T *r = in.f[F_R], *u = in.f[F_U], *v = in.f[F_V], *w = in.f[F_W];
-    const long long c = g.at(x, y, z);
-    const long long xe = g.at(x + 1, y, z), xw = g.at(x - 1, y, z);
-    const long long yn = g.at(x, y + 1, z), ys = g.at(x, y - 1, z);
-    const long long zu = g.at(x, y, z + 1), zd = g.at(x, y, z - 1);
-    const T div = T(0.5) * ((rho0 + r[xe]) * u[xe] - (rho0 + r[xw]) * u[xw]) +
-                  T(0.5) * ((rho0 + r[yn]) * v[yn] - (rho0 + r[ys]) * v[ys]) +
-                  T(0.5) * ((rho0 + r[zu]) * w[zu] - (rho0 + r[zd]) * w[zd]);
-    const T lap = (r[xe] + r[xw]) + (r[yn] + r[ys]) + (r[zu] + r[zd]) - T(6) * r[c];
+    const Axis7 a(g, x, y, z);
+    const T div = T(0.5) * ((rho0 + r[a.xe]) * u[a.xe] - (rho0 + r[a.xw]) * u[a.xw]) +
+                  T(0.5) * ((rho0 + r[a.yn]) * v[a.yn] - (rho0 + r[a.ys]) * v[a.ys]) +
+                  T(0.5) * ((rho0 + r[a.zu]) * w[a.zu] - (rho0 + r[a.zd]) * w[a.zd]);
+    const T lap = (r[a.xe] + r[a.xw]) + (r[a.yn] + r[a.ys]) + (r[a.zu] + r[a.zd]) - T(6) * r[a.c];
     return -dt * div + satc * lap;
 }
 
@@ -184,25 +227,28 @@ __global__ void __launch_bounds__(TPB) k_drho(const RunDesc R, Fields<T> in, T *
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z * blockDim.z + threadIdx.z;
     if (x < g.nx && y < g.ny && z < g.nz) do {  // one node per thread
-        const long long c = g.at(x, y, z);
+        const long long c = g.base + (long long)z * g.pxy + (long long)y * g.px + x;
         if (!g.wall(z)) {
             dr[c] = drho_at(in, g, x, y, z, rho0, dt, satc);
             continue;
         }
         const int s = z == 0 ? 1 : -1;
         const T *r = in.f[F_R];
-        const T r1 = r[g.at(x, y, z + s)] + drho_at(in, g, x, y, z + s, rho0, dt, satc);
-        const T r2 = r[g.at(x, y, z + 2 * s)] + drho_at(in, g, x, y, z + 2 * s, rho0, dt, satc);
+        const T r1 = r[c + s * g.pxy] + drho_at(in, g, x, y, z + s, rho0, dt, satc);
+        const T r2 = r[c + 2 * s * g.pxy] + drho_at(in, g, x, y, z + 2 * s, rho0, dt, satc);
         dr[c] = (T(4) * r1 - r2) / T(3) - r[c];
     } while (0);
 }
 
-// 3: rho^{n+1}, u^{n+1} and phi*
+// 3: rho^{n+1}, u^{n+1} and phi*.  mu and phi (D3Q19 stencils) come from
+// the shared-memory plane windows of the z-march; rho', u, v, w and
+// Delta rho (7-point stencils) through L1 (staging them too was slower).
 template <typename T>
-__global__ void __launch_bounds__(TPB)
+__global__ void __launch_bounds__(BX *BY)
     k_main(const RunDesc R, Fields<T> in, Fields<T> out, const T *__restrict__ dr,
            const T *__restrict__ mu, T *__restrict__ phs, unsigned *err)
 {
+    __shared__ T wmu[3][WP], wph[3][WP];
     const Geo3 g(R);
     const T *C = coefs<T>(R);
     const T rho0 = C[C_RHO0], dt = C[C_DT], cs2 = C[C_CS2], nudt = C[C_NUDT];
@@ -210,23 +256,27 @@ __global__ void __launch_bounds__(TPB)
     const T gfx = C[C_GX], gfy = C[C_GY], gfz = C[C_GZ];
     const T *r = in.f[F_R], *u = in.f[F_U], *v = in.f[F_V], *w = in.f[F_W], *ph = in.f[F_PHI];
     bool bad = false;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z * blockDim.z + threadIdx.z;
-    if (x < g.nx && y < g.ny && z < g.nz) do {  // one node per thread
-        const Hood h(g, x, y, z);
-        const long long c = h.zo[1] + h.yo[1] + h.xo[1];
+    const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    const int cw = (threadIdx.y + 1) * WX + threadIdx.x + 1;
+    zmarch(g.nz,
+           [&](int sl, int z) {
+               load_window<T, K_MIRROR>(wmu[sl], mu, g, x0, y0, z, T(0));
+               load_window<T, K_WET>(wph[sl], ph, g, x0, y0, z, wet);
+           },
+           [&](int z, int sm, int s0, int sp) {
+        if (x >= g.nx || y >= g.ny) return;
+        const Axis7 ax(g, x, y, z);
+        const long long c = ax.c;
         const T r0 = r[c], d0 = dr[c];
         const T rho1 = rho0 + r0 + d0;
-        const T u0 = u[c], v0 = v[c], w0 = w[c], f0 = ph[c];
+        const T u0 = u[c], v0 = v[c], w0 = w[c], f0 = wph[s0][cw];
         // mu^n: Laplacian for the CHE and gradient for F_ST
         T lmu, gmx, gmy, gmz;
-        iso_ops<T, K_MIRROR>(mu, h, T(0), mu[c], lmu, gmx, gmy, gmz);
+        iso_ops(wmu[sm], wmu[s0], wmu[sp], cw, lmu, gmx, gmy, gmz);
         T un = T(0), vn = T(0), wn = T(0);
         if (!g.wall(z)) {
-            const long long nb[6] = {h.zo[1] + h.yo[1] + h.xo[2], h.zo[1] + h.yo[1] + h.xo[0],
-                                     h.zo[1] + h.yo[2] + h.xo[1], h.zo[1] + h.yo[0] + h.xo[1],
-                                     h.zo[2] + h.yo[1] + h.xo[1], h.zo[0] + h.yo[1] + h.xo[1]};
+            const long long nb[6] = {ax.xe, ax.xw, ax.yn, ax.ys, ax.zu, ax.zd};
             T q[6], mx[6], my[6], mz[6];
 #pragma unroll
             for (int k = 0; k < 6; ++k) {
@@ -262,7 +312,7 @@ __global__ void __launch_bounds__(TPB)
         }
         // first Heun stage of Eq. (2.14), u^n frozen
         T lph, gpx, gpy, gpz;
-        iso_ops<T, K_WET>(ph, h, wet, f0, lph, gpx, gpy, gpz);
+        iso_ops(wph[sm], wph[s0], wph[sp], cw, lph, gpx, gpy, gpz);
         const T fs = f0 + dt * (-(u0 * gpx + v0 * gpy + w0 * gpz) + mob * lmu);
         const T rn = r0 + d0;
         out.f[F_R][c] = rn;
@@ -271,35 +321,41 @@ __global__ void __launch_bounds__(TPB)
         out.f[F_W][c] = wn;
         phs[c] = fs;
         bad |= !isfinite(rn + un + vn + wn + fs);
-    } while (0);
+           });
     if (bad) atomicOr(err, ERR_NONFINITE);
 }
 
 // 5: phi^{n+1}
 template <typename T>
-__global__ void __launch_bounds__(TPB)
+__global__ void __launch_bounds__(BX *BY)
     k_phi(const RunDesc R, Fields<T> in, const T *__restrict__ phs, const T *__restrict__ mus,
           T *__restrict__ phn, unsigned *err)
 {
+    __shared__ T wmu[3][WP], wps[3][WP];
     const Geo3 g(R);
     const T *C = coefs<T>(R);
     const T dt = C[C_DT], mob = C[C_M], wet = C[C_WET];
     const T *u = in.f[F_U], *v = in.f[F_V], *w = in.f[F_W], *ph = in.f[F_PHI];
     bool bad = false;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z * blockDim.z + threadIdx.z;
-    if (x < g.nx && y < g.ny && z < g.nz) do {  // one node per thread
-        const Hood h(g, x, y, z);
-        const long long c = h.zo[1] + h.yo[1] + h.xo[1];
-        T lmu, a0, a1, a2, lph, gpx, gpy, gpz;
-        iso_ops<T, K_MIRROR>(mus, h, T(0), mus[c], lmu, a0, a1, a2);
-        iso_ops<T, K_WET>(phs, h, wet, phs[c], lph, gpx, gpy, gpz);
-        const T r2 = -(u[c] * gpx + v[c] * gpy + w[c] * gpz) + mob * lmu;
-        const T f = T(0.5) * (ph[c] + phs[c] + dt * r2);
-        phn[c] = f;
-        bad |= !isfinite(f);
-    } while (0);
+    const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    const int cw = (threadIdx.y + 1) * WX + threadIdx.x + 1;
+    zmarch(g.nz,
+           [&](int sl, int z) {
+               load_window<T, K_MIRROR>(wmu[sl], mus, g, x0, y0, z, T(0));
+               load_window<T, K_WET>(wps[sl], phs, g, x0, y0, z, wet);
+           },
+           [&](int z, int sm, int s0, int sp) {
+               if (x >= g.nx || y >= g.ny) return;
+               const long long c = g.base + (long long)z * g.pxy + (long long)y * g.px + x;
+               T lmu, a0, a1, a2, lph, gpx, gpy, gpz;
+               iso_ops(wmu[sm], wmu[s0], wmu[sp], cw, lmu, a0, a1, a2);
+               iso_ops(wps[sm], wps[s0], wps[sp], cw, lph, gpx, gpy, gpz);
+               const T r2 = -(u[c] * gpx + v[c] * gpy + w[c] * gpz) + mob * lmu;
+               const T f = T(0.5) * (ph[c] + wps[s0][cw] + dt * r2);
+               phn[c] = f;
+               bad |= !isfinite(f);
+           });
     if (bad) atomicOr(err, ERR_NONFINITE);
 }
 
@@ -310,14 +366,17 @@ cudaError_t launch_tp3d(const RunDesc &R, Fields<T> in, Fields<T> out, T *mu, T 
                         unsigned *err, int sms, cudaStream_t s)
 {
     (void)sms;
-    // one thread per node: 32 x 4 x 2 blocks (x fastest, coalesced rows)
+    // Delta rho: one thread per node, 32 x 4 x 2 blocks (x fastest, coalesced)
     const dim3 blk(32, 4, 2);
     const dim3 grid((R.nx + 31) / 32, (R.ny + 3) / 4, (R.nz + 1) / 2);
-    k_mu<T><<<grid, blk, 0, s>>>(R, in.f[F_PHI], mu);
+    // D3Q19 passes: BX x BY tiles marching over chunks of ZCH planes
+    const dim3 tblk(BX, BY, 1);
+    const dim3 tgrid((R.nx + BX - 1) / BX, (R.ny + BY - 1) / BY, (R.nz + ZCH - 1) / ZCH);
+    k_mu<T><<<tgrid, tblk, 0, s>>>(R, in.f[F_PHI], mu);
     k_drho<T><<<grid, blk, 0, s>>>(R, in, dr);
-    k_main<T><<<grid, blk, 0, s>>>(R, in, out, dr, mu, phs, err);
-    k_mu<T><<<grid, blk, 0, s>>>(R, phs, mu);
-    k_phi<T><<<grid, blk, 0, s>>>(R, in, phs, mu, out.f[F_PHI], err);
+    k_main<T><<<tgrid, tblk, 0, s>>>(R, in, out, dr, mu, phs, err);
+    k_mu<T><<<tgrid, tblk, 0, s>>>(R, phs, mu);
+    k_phi<T><<<tgrid, tblk, 0, s>>>(R, in, phs, mu, out.f[F_PHI], err);
     return cudaGetLastError();
 }
 
