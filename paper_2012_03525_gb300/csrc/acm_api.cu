@@ -423,6 +423,9 @@ acm_status create_common(const acm_params *params, int nruns, acm_handle **out)
             if (h->prec == ACM_FP64) mames2d_max_blocks_per_sm<double>();
             else mames2d_max_blocks_per_sm<float>();
         }
+    } else if (h->two_phase) {
+        if (h->prec == ACM_FP64) tp3d_prepare<double>();
+        else tp3d_prepare<float>();
     } else {
         for (int t3y : {8, 16}) {
             if (h->prec == ACM_FP64) step3d_max_blocks_per_sm<double>(t3y);

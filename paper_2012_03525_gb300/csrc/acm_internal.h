@@ -107,6 +107,8 @@ cudaError_t launch_reduce(const RunDesc *druns, int nruns, int dim, Fields<T> cu
 // 3D two-phase step (five launches: mu, Delta rho, momentum + phi*, mu*,
 // phi^{n+1}); mu, phs, dr are scratch fields of the run's storage size.
 template <typename T>
+void tp3d_prepare();  // launch attributes of the 3D two-phase step (before any capture)
+template <typename T>
 cudaError_t launch_tp3d(const RunDesc &R, Fields<T> in, Fields<T> out, T *mu, T *phs, T *dr,
                         unsigned *err, int sms, cudaStream_t s);
 

@@ -102,30 +102,47 @@ struct Axis7 {
     }
 };
 
-// window of plane z (z in [-1, nz]) of field f around the tile at (x0, y0):
-// x and y wrap; beyond a wall face the mirror plane, plus (KIND == K_WET)
-// the wetting term wet (1 - f_w^2) of the wall plane
+// The x-y part of the storage offsets of the window elements a thread loads
+// (elements tid and tid + BX BY of the WX x WY window; x and y wrap): the
+// same for every field and plane, so it is formed once per CTA.
+struct WinXY {
+    long long xy[2];
+    bool has2;
+    __device__ __forceinline__ WinXY(const Geo3 &g, int x0, int y0)
+    {
+        const int tid = threadIdx.y * BX + threadIdx.x;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int i = min(tid + k * BX * BY, WP - 1);
+            const int wy = i / WX, wx = i - wy * WX;
+            xy[k] = g.base + (long long)wrapc(y0 - 1 + wy, g.ny) * g.px + wrapc(x0 - 1 + wx, g.nx);
+        }
+        has2 = tid + BX * BY < WP;
+    }
+};
+static_assert(WP <= 2 * BX * BY, "a window must fit two loads per thread");
+
+// window of plane z (z in [-1, nz]) of field f: beyond a wall face the
+// mirror plane, plus (KIND == K_WET) the wetting term wet (1 - f_w^2) of the
+// wall plane
 template <typename T, int KIND>
 __device__ __forceinline__ void load_window(T *dst, const T *__restrict__ f, const Geo3 &g,
-                                            int x0, int y0, int z, T wet)
+                                            const WinXY &o, int z, T wet)
 {
     const int tid = threadIdx.y * BX + threadIdx.x;
-    for (int i = tid; i < WP; i += BX * BY) {
-        const int wy = i / WX, wx = i - wy * WX;
-        const int xx = wrapc(x0 - 1 + wx, g.nx), yy = wrapc(y0 - 1 + wy, g.ny);
-        const long long xy = g.base + (long long)yy * g.px + xx;
-        T val;
-        if (g.zwall && (z < 0 || z >= g.nz)) {
-            const int zm = z < 0 ? 1 : g.nz - 2, zw = z < 0 ? 0 : g.nz - 1;
-            val = f[xy + (long long)zm * g.pxy];
-            if (KIND == K_WET) {
-                const T fw = f[xy + (long long)zw * g.pxy];
-                val += wet * (T(1) - fw * fw);
-            }
-        } else {
-            val = f[xy + (long long)(g.zwall ? z : g.wz(z)) * g.pxy];
+    const bool ghost = g.zwall && (z < 0 || z >= g.nz);
+    const int zz = ghost ? (z < 0 ? 1 : g.nz - 2) : (g.zwall ? z : g.wz(z));
+    const long long zo = (long long)zz * g.pxy;
+    const long long zwo = (long long)(z < 0 ? 0 : g.nz - 1) * g.pxy;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        if (k == 1 && !o.has2) break;
+        T val = f[o.xy[k] + zo];
+        if (KIND == K_WET && ghost) {
+            const T fw = f[o.xy[k] + zwo];
+            val += wet * (T(1) - fw * fw);
         }
-        dst[i] = val;
+        dst[tid + k * BX * BY] = val;
     }
 }
 
@@ -190,8 +207,9 @@ __global__ void __launch_bounds__(BX *BY) k_mu(const RunDesc R, const T *__restr
     const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
     const int c = (threadIdx.y + 1) * WX + threadIdx.x + 1;
+    const WinXY o(g, x0, y0);
     zmarch(
-        g.nz, [&](int sl, int z) { load_window<T, K_WET>(win[sl], phi, g, x0, y0, z, wet); },
+        g.nz, [&](int sl, int z) { load_window<T, K_WET>(win[sl], phi, g, o, z, wet); },
         [&](int z, int sm, int s0, int sp) {
             if (x >= g.nx || y >= g.ny) return;
             T lap, gx, gy, gz;
@@ -240,70 +258,91 @@ __global__ void __launch_bounds__(TPB) k_drho(const RunDesc R, Fields<T> in, T *
     } while (0);
 }
 
-// 3: rho^{n+1}, u^{n+1} and phi*.  mu and phi (D3Q19 stencils) come from
-// the shared-memory plane windows of the z-march; rho', u, v, w and
-// Delta rho (7-point stencils) through L1 (staging them too was slower).
+// 3: rho^{n+1}, u^{n+1} and phi*.  Every operand (mu, phi with the D3Q19
+// stencils; rho', u, v, w, Delta rho with the 7-point ones) comes from the
+// shared-memory plane windows of the z-march.
+enum { W_MU, W_PH, W_R, W_U, W_V, W_W, W_DR, NWIN };
+
+template <typename T>
+constexpr size_t main_smem()
+{
+    return sizeof(T) * NWIN * 3 * WP;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(BX *BY)
     k_main(const RunDesc R, Fields<T> in, Fields<T> out, const T *__restrict__ dr,
            const T *__restrict__ mu, T *__restrict__ phs, unsigned *err)
 {
-    __shared__ T wmu[3][WP], wph[3][WP];
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T *sw = reinterpret_cast<T *>(smraw);
+    auto win = [&](int f, int slot) { return sw + (f * 3 + slot) * WP; };
     const Geo3 g(R);
     const T *C = coefs<T>(R);
     const T rho0 = C[C_RHO0], dt = C[C_DT], cs2 = C[C_CS2], nudt = C[C_NUDT];
     const T satm = C[C_SATM], mob = C[C_M], wet = C[C_WET];
     const T gfx = C[C_GX], gfy = C[C_GY], gfz = C[C_GZ];
-    const T *r = in.f[F_R], *u = in.f[F_U], *v = in.f[F_V], *w = in.f[F_W], *ph = in.f[F_PHI];
+    const T *src[NWIN] = {mu, in.f[F_PHI], in.f[F_R], in.f[F_U], in.f[F_V], in.f[F_W], dr};
     bool bad = false;
     const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
     const int cw = (threadIdx.y + 1) * WX + threadIdx.x + 1;
+    const WinXY o(g, x0, y0);
     zmarch(g.nz,
            [&](int sl, int z) {
-               load_window<T, K_MIRROR>(wmu[sl], mu, g, x0, y0, z, T(0));
-               load_window<T, K_WET>(wph[sl], ph, g, x0, y0, z, wet);
+#pragma unroll
+               for (int f = 0; f < NWIN; ++f) {
+                   if (f == W_PH) load_window<T, K_WET>(win(f, sl), src[f], g, o, z, wet);
+                   else load_window<T, K_MIRROR>(win(f, sl), src[f], g, o, z, T(0));
+               }
            },
            [&](int z, int sm, int s0, int sp) {
         if (x >= g.nx || y >= g.ny) return;
-        const Axis7 ax(g, x, y, z);
-        const long long c = ax.c;
-        const T r0 = r[c], d0 = dr[c];
+        const T *r = win(W_R, s0), *u = win(W_U, s0), *v = win(W_V, s0), *w = win(W_W, s0);
+        const T *d = win(W_DR, s0);
+        const T r0 = r[cw], d0 = d[cw];
         const T rho1 = rho0 + r0 + d0;
-        const T u0 = u[c], v0 = v[c], w0 = w[c], f0 = wph[s0][cw];
+        const T u0 = u[cw], v0 = v[cw], w0 = w[cw], f0 = win(W_PH, s0)[cw];
         // mu^n: Laplacian for the CHE and gradient for F_ST
         T lmu, gmx, gmy, gmz;
-        iso_ops(wmu[sm], wmu[s0], wmu[sp], cw, lmu, gmx, gmy, gmz);
+        iso_ops(win(W_MU, sm), win(W_MU, s0), win(W_MU, sp), cw, lmu, gmx, gmy, gmz);
         T un = T(0), vn = T(0), wn = T(0);
         if (!g.wall(z)) {
-            const long long nb[6] = {ax.xe, ax.xw, ax.yn, ax.ys, ax.zu, ax.zd};
-            T q[6], mx[6], my[6], mz[6];
+            // neighbours E, W, N, S in plane z; U, D in the planes above/below
+            const T rr[6] = {r[cw + 1], r[cw - 1], r[cw + WX], r[cw - WX], win(W_R, sp)[cw],
+                             win(W_R, sm)[cw]};
+            const T uu[6] = {u[cw + 1], u[cw - 1], u[cw + WX], u[cw - WX], win(W_U, sp)[cw],
+                             win(W_U, sm)[cw]};
+            const T vv[6] = {v[cw + 1], v[cw - 1], v[cw + WX], v[cw - WX], win(W_V, sp)[cw],
+                             win(W_V, sm)[cw]};
+            const T ww[6] = {w[cw + 1], w[cw - 1], w[cw + WX], w[cw - WX], win(W_W, sp)[cw],
+                             win(W_W, sm)[cw]};
+            T mx[6], my[6], mz[6];
 #pragma unroll
             for (int k = 0; k < 6; ++k) {
-                q[k] = rho0 + r[nb[k]];
-                mx[k] = q[k] * u[nb[k]];
-                my[k] = q[k] * v[nb[k]];
-                mz[k] = q[k] * w[nb[k]];
+                const T q = rho0 + rr[k];
+                mx[k] = q * uu[k];
+                my[k] = q * vv[k];
+                mz[k] = q * ww[k];
             }
             const T q0 = rho0 + r0;
             const T mx0 = q0 * u0, my0 = q0 * v0, mz0 = q0 * w0;
             auto flux = [&](const T (&m)[6]) {
-                return T(0.5) * ((m[0] * u[nb[0]] - m[1] * u[nb[1]]) +
-                                 (m[2] * v[nb[2]] - m[3] * v[nb[3]]) +
-                                 (m[4] * w[nb[4]] - m[5] * w[nb[5]]));
+                return T(0.5) * ((m[0] * uu[0] - m[1] * uu[1]) + (m[2] * vv[2] - m[3] * vv[3]) +
+                                 (m[4] * ww[4] - m[5] * ww[5]));
             };
             auto lap = [&](const T (&m)[6], T m0) {
                 return ((m[0] + m[1]) + (m[2] + m[3])) + (m[4] + m[5]) - T(6) * m0;
             };
-            const T ddx = T(0.5) * (dr[nb[0]] - dr[nb[1]]);
-            const T ddy = T(0.5) * (dr[nb[2]] - dr[nb[3]]);
-            const T ddz = T(0.5) * (dr[nb[4]] - dr[nb[5]]);
+            const T ddx = T(0.5) * (d[cw + 1] - d[cw - 1]);
+            const T ddy = T(0.5) * (d[cw + WX] - d[cw - WX]);
+            const T ddz = T(0.5) * (win(W_DR, sp)[cw] - win(W_DR, sm)[cw]);
             const T fb = dt * rho1;
-            T rx = -dt * flux(mx) - dt * cs2 * T(0.5) * (r[nb[0]] - r[nb[1]]) + nudt * lap(mx, mx0) -
+            T rx = -dt * flux(mx) - dt * cs2 * T(0.5) * (rr[0] - rr[1]) + nudt * lap(mx, mx0) -
                    satm * ddx + fb * gfx - dt * f0 * gmx;
-            T ry = -dt * flux(my) - dt * cs2 * T(0.5) * (r[nb[2]] - r[nb[3]]) + nudt * lap(my, my0) -
+            T ry = -dt * flux(my) - dt * cs2 * T(0.5) * (rr[2] - rr[3]) + nudt * lap(my, my0) -
                    satm * ddy + fb * gfy - dt * f0 * gmy;
-            T rz = -dt * flux(mz) - dt * cs2 * T(0.5) * (r[nb[4]] - r[nb[5]]) + nudt * lap(mz, mz0) -
+            T rz = -dt * flux(mz) - dt * cs2 * T(0.5) * (rr[4] - rr[5]) + nudt * lap(mz, mz0) -
                    satm * ddz + fb * gfz - dt * f0 * gmz;
             const T inv = T(1) / rho1;
             un = u0 + (rx - d0 * u0) * inv;
@@ -312,9 +351,10 @@ __global__ void __launch_bounds__(BX *BY)
         }
         // first Heun stage of Eq. (2.14), u^n frozen
         T lph, gpx, gpy, gpz;
-        iso_ops(wph[sm], wph[s0], wph[sp], cw, lph, gpx, gpy, gpz);
+        iso_ops(win(W_PH, sm), win(W_PH, s0), win(W_PH, sp), cw, lph, gpx, gpy, gpz);
         const T fs = f0 + dt * (-(u0 * gpx + v0 * gpy + w0 * gpz) + mob * lmu);
         const T rn = r0 + d0;
+        const long long c = g.base + (long long)z * g.pxy + (long long)y * g.px + x;
         out.f[F_R][c] = rn;
         out.f[F_U][c] = un;
         out.f[F_V][c] = vn;
@@ -340,10 +380,11 @@ __global__ void __launch_bounds__(BX *BY)
     const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
     const int cw = (threadIdx.y + 1) * WX + threadIdx.x + 1;
+    const WinXY o(g, x0, y0);
     zmarch(g.nz,
            [&](int sl, int z) {
-               load_window<T, K_MIRROR>(wmu[sl], mus, g, x0, y0, z, T(0));
-               load_window<T, K_WET>(wps[sl], phs, g, x0, y0, z, wet);
+               load_window<T, K_MIRROR>(wmu[sl], mus, g, o, z, T(0));
+               load_window<T, K_WET>(wps[sl], phs, g, o, z, wet);
            },
            [&](int z, int sm, int s0, int sp) {
                if (x >= g.nx || y >= g.ny) return;
@@ -362,6 +403,13 @@ __global__ void __launch_bounds__(BX *BY)
 }  // namespace
 
 template <typename T>
+void tp3d_prepare()
+{
+    cudaFuncSetAttribute(k_main<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)main_smem<T>());
+}
+
+template <typename T>
 cudaError_t launch_tp3d(const RunDesc &R, Fields<T> in, Fields<T> out, T *mu, T *phs, T *dr,
                         unsigned *err, int sms, cudaStream_t s)
 {
@@ -374,12 +422,14 @@ cudaError_t launch_tp3d(const RunDesc &R, Fields<T> in, Fields<T> out, T *mu, T 
     const dim3 tgrid((R.nx + BX - 1) / BX, (R.ny + BY - 1) / BY, (R.nz + ZCH - 1) / ZCH);
     k_mu<T><<<tgrid, tblk, 0, s>>>(R, in.f[F_PHI], mu);
     k_drho<T><<<grid, blk, 0, s>>>(R, in, dr);
-    k_main<T><<<tgrid, tblk, 0, s>>>(R, in, out, dr, mu, phs, err);
+    k_main<T><<<tgrid, tblk, main_smem<T>(), s>>>(R, in, out, dr, mu, phs, err);
     k_mu<T><<<tgrid, tblk, 0, s>>>(R, phs, mu);
     k_phi<T><<<tgrid, tblk, 0, s>>>(R, in, phs, mu, out.f[F_PHI], err);
     return cudaGetLastError();
 }
 
+template void tp3d_prepare<float>();
+template void tp3d_prepare<double>();
 template cudaError_t launch_tp3d<float>(const RunDesc &, Fields<float>, Fields<float>, float *,
                                         float *, float *, unsigned *, int, cudaStream_t);
 template cudaError_t launch_tp3d<double>(const RunDesc &, Fields<double>, Fields<double>,
