@@ -137,8 +137,16 @@ __device__ __forceinline__ void load_window(T *dst, const T *__restrict__ f, con
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         if (k == 1 && !o.has2) break;
+        if (!ghost) {  // a plain copy: asynchronous, completed by the z-march's wait
+            const unsigned d =
+                static_cast<unsigned>(__cvta_generic_to_shared(dst + tid + k * BX * BY));
+            asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d),
+                         "l"(f + o.xy[k] + zo), "n"(sizeof(T))
+                         : "memory");
+            continue;
+        }
         T val = f[o.xy[k] + zo];
-        if (KIND == K_WET && ghost) {
+        if (KIND == K_WET) {
             const T fw = f[o.xy[k] + zwo];
             val += wet * (T(1) - fw * fw);
         }
@@ -178,21 +186,30 @@ __device__ __forceinline__ void iso_ops(const T *wm, const T *w0, const T *wp, i
     gz = T(1.0 / 6.0) * az + T(1.0 / 12.0) * ez;
 }
 
-// Walk the CTA's z-chunk: `load(slot, z)` fills the windows of plane z,
-// `body(z, sm, s0, sp)` computes plane z from the slots of z-1, z, z+1
+// Walk the CTA's z-chunk: `load(slot, z)` issues the copies of plane z into
+// ring slot `slot` (NSL slots), `body(z, sm, s0, sp)` computes plane z from
+// the slots of z-1, z, z+1.  Plane z+2 is in flight while plane z is
+// computed (cp.async groups, one per plane).
+constexpr int NSL = 4;
 template <typename L, typename B>
 __device__ __forceinline__ void zmarch(int nz, L load, B body)
 {
     const int z0 = blockIdx.z * ZCH, zend = min(z0 + ZCH, nz);
     load(0, z0 - 1);
     load(1, z0);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    load(2, z0 + 1);
+    asm volatile("cp.async.commit_group;" ::: "memory");
     for (int z = z0; z < zend; ++z) {
         const int k = z - z0;
-        load((k + 2) % 3, z + 1);
+        if (z + 2 <= zend) load((k + 3) % NSL, z + 2);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 1;" ::: "memory");  // planes up to z+1 landed
         __syncthreads();
-        body(z, k % 3, (k + 1) % 3, (k + 2) % 3);
-        __syncthreads();  // slot k % 3 is refilled next
+        body(z, k % NSL, (k + 1) % NSL, (k + 2) % NSL);
+        __syncthreads();  // slot k % NSL is refilled next
     }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
 // 1, 4: mu = 4 a phi (phi^2 - 1) - kappa Lap_iso(phi)
@@ -200,7 +217,7 @@ template <typename T>
 __global__ void __launch_bounds__(BX *BY) k_mu(const RunDesc R, const T *__restrict__ phi,
                                                T *__restrict__ mu)
 {
-    __shared__ T win[3][WP];
+    __shared__ T win[NSL][WP];
     const Geo3 g(R);
     const T *C = coefs<T>(R);
     const T a = C[C_A], kappa = C[C_KAPPA], wet = C[C_WET];
@@ -266,7 +283,7 @@ enum { W_MU, W_PH, W_R, W_U, W_V, W_W, W_DR, NWIN };
 template <typename T>
 constexpr size_t main_smem()
 {
-    return sizeof(T) * NWIN * 3 * WP;
+    return sizeof(T) * NWIN * NSL * WP;
 }
 
 template <typename T>
@@ -276,7 +293,7 @@ __global__ void __launch_bounds__(BX *BY)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     T *sw = reinterpret_cast<T *>(smraw);
-    auto win = [&](int f, int slot) { return sw + (f * 3 + slot) * WP; };
+    auto win = [&](int f, int slot) { return sw + (f * NSL + slot) * WP; };
     const Geo3 g(R);
     const T *C = coefs<T>(R);
     const T rho0 = C[C_RHO0], dt = C[C_DT], cs2 = C[C_CS2], nudt = C[C_NUDT];
@@ -371,7 +388,7 @@ __global__ void __launch_bounds__(BX *BY)
     k_phi(const RunDesc R, Fields<T> in, const T *__restrict__ phs, const T *__restrict__ mus,
           T *__restrict__ phn, unsigned *err)
 {
-    __shared__ T wmu[3][WP], wps[3][WP];
+    __shared__ T wmu[NSL][WP], wps[NSL][WP];
     const Geo3 g(R);
     const T *C = coefs<T>(R);
     const T dt = C[C_DT], mob = C[C_M], wet = C[C_WET];
