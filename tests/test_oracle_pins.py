@@ -604,6 +604,29 @@ def test_capillary_wave_analytic_period_matches_table():
         assert first == pytest.approx(tab[key], rel=2e-3)
 
 
+def test_capillary_wave_unstable_at_c5_stable_at_c6(oracle_lib):
+    """Section 3.4: at Re = 1000, Cn = 0.0625, Pe = 2e4 the capillary wave
+    runs stably at c = 6 and becomes unstable when c is lowered to 5 (the
+    Cahn-Hilliard step constrains the time step).  Here: c = 5 blows up
+    within 3 T_c, c = 6 stays bounded over 6 T_c."""
+    co = oracle_lib
+    out = {}
+    for c, periods in ((5.0, 3), (6.0, 6)):
+        cw = wl.CapillaryWave(n_l=64, c=c, re=1000.0, cn=0.0625)
+        rho, u, v, phi = cw.initial()
+        p = co.make_params(cw.shape, nu=cw.nu, bc=[0, 0, 1, 1, 0, 0], two_phase=True,
+                           sigma=cw.sigma, W=cw.W, M=cw.M)
+        stable = True
+        for _ in range(periods):
+            with np.errstate(all="ignore"):
+                co.step(p, rho, u, v, None, phi, nsteps=int(cw.steps_per_tc))
+            if not np.isfinite(u).all() or np.abs(u).max() > 1.0:
+                stable = False
+                break
+        out[c] = stable
+    assert out == {5.0: False, 6.0: True}
+
+
 @pytest.mark.slow
 def test_capillary_wave_period_oracle(oracle_lib):
     """Section 3.4 capillary wave at Re = 1000, N_L = 64, c = 6, Cn = 0.0625,

@@ -178,3 +178,24 @@ def test_capillary_wave_periods_table2(re, key):
     assert coarse == pytest.approx(exact, rel=0.07)
     assert fine == pytest.approx(exact, rel=0.03)
     assert abs(fine - exact) < abs(coarse - exact)
+
+
+def test_capillary_wave_unstable_at_c5_on_gpu():
+    """Section 3.4: the capillary wave (Re = 1000, N_L = 64, Cn = 0.0625,
+    Pe = 2e4) blows up at c = 5 -- reported as ACM_EUNSTABLE -- and runs at
+    c = 6."""
+    out = {}
+    for c in (5.0, 6.0):
+        cw = wl.CapillaryWave(n_l=64, c=c, re=1000.0, cn=0.0625)
+        p = acm.make_params(cw.shape, nu=cw.nu, bc=[0, 0, 1, 1, 0, 0], two_phase=True,
+                            sigma=cw.sigma, W=cw.W, M=cw.M)
+        with acm.Solver(p) as s:
+            s.set_fields(*cw.initial()[:3], None, cw.initial()[3])
+            s.step(int(6 * cw.steps_per_tc))
+            try:
+                s.sync()
+                out[c] = bool(np.abs(s.fields()[1]).max() < 1.0)
+            except acm.AcmError as e:
+                assert e.status == acm.EUNSTABLE
+                out[c] = False
+    assert out == {5.0: False, 6.0: True}
