@@ -70,7 +70,10 @@ __host__ __device__ __forceinline__ const double *coefs<double>(const RunDesc &R
 
 // 2D tile geometry (outputs per tile).
 constexpr int T2X = 32;
-constexpr int T2Y = 16;
+#ifndef ACM_T2Y
+#define ACM_T2Y 32
+#endif
+constexpr int T2Y = ACM_T2Y;
 constexpr int T2THREADS = 256;
 
 // 3D z-marching kernel geometry.

@@ -12,7 +12,7 @@
 // d_aa, the centred four-point mixed difference for d_xy.
 //
 // One kernel per step, no intermediate fields in memory: a CTA stages its
-// 32 x 16 tile of rho', u, v with a two-node halo in shared memory, forms
+// 32 x 32 tile of rho', u, v with a two-node halo in shared memory, forms
 // m = rho u and Pi on the staged window, evaluates the predictor on the tile
 // grown by one node (the corrector's differences of Pi* reach one node),
 // keeps the increments Delta rho, Delta m and Pi* - Pi there, and applies
