@@ -40,15 +40,22 @@ __device__ __forceinline__ int wrap_p(int c, int n)
     return c;
 }
 
+// Visit a (RW x RH) window, 32 <= RW <= 64: warp w takes the first 32
+// columns of rows w, w + 8, ...; the remaining RW - 32 columns of every row
+// are packed into full warps as one flat list, handed out starting at the
+// first warp with one row fewer.
 template <int RW, int RH, typename F>
 __device__ __forceinline__ void for_window(F f)
 {
+    static_assert(RW >= 32 && RW <= 64, "window width");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int ly = warp; ly < RH; ly += NWARP) {
-#pragma unroll
-        for (int lx0 = 0; lx0 < RW; lx0 += 32) {
-            const int lx = lx0 + lane;
-            if (lx < RW) f(ly, lx);
+    for (int ly = warp; ly < RH; ly += NWARP) f(ly, lane);
+    if constexpr (RW > 32) {
+        constexpr int TW = RW - 32, NT = RH * TW;
+        const int t0 = (threadIdx.x + T2THREADS - (RH % NWARP) * 32) % T2THREADS;
+        for (int t = t0; t < NT; t += T2THREADS) {
+            const int ly = t / TW;
+            f(ly, 32 + (t - ly * TW));
         }
     }
 }
@@ -83,9 +90,10 @@ __global__ void __launch_bounds__(T2THREADS)
 
         __syncthreads();  // shared memory of the previous item is free
         {
-            const int ca = wrap_p(x0 - 2 + lane, nx), cb = wrap_p(x0 - 2 + lane + 32, nx);
+            const int ca = wrap_p(x0 - 2 + lane, nx);
             for_window<RW2, RH2>([&](int ly, int lx) {
-                const long long k = (long long)wrap_p(y0 - 2 + ly, ny) * nx + (lx < 32 ? ca : cb);
+                const long long k = (long long)wrap_p(y0 - 2 + ly, ny) * nx +
+                                    (lx < 32 ? ca : wrap_p(x0 - 2 + lx, nx));
                 const int i = ly * RW2 + lx;
                 const T r = gr[k], u = gu[k], v = gv[k];
                 const T mx = (rho0 + r) * u, my = (rho0 + r) * v;

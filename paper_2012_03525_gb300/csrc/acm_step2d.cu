@@ -54,23 +54,27 @@ __device__ __forceinline__ int wrap_or_clamp(int c, int n, bool periodic)
     return c < 0 ? 0 : (c >= n ? n - 1 : c);
 }
 
-// Visit a (RW x RH) window row by row: warp w takes rows w, w + 8, ...; a
-// lane takes columns lane and lane + 32.  Consecutive lanes touch
-// consecutive shared-memory words (no bank conflicts) and the row index is
-// computed once per row.
+// Visit a (RW x RH) window, 32 <= RW <= 64: warp w takes the first 32
+// columns of rows w, w + 8, ... (lane = column: consecutive lanes touch
+// consecutive shared-memory words); the remaining RW - 32 columns of every
+// row are packed into full warps as one flat list (element t: row t / TW,
+// column 32 + t % TW), handed out starting at the first warp with one row
+// fewer, so that no warp issues an instruction for a handful of lanes.
 template <int RW, int RH, typename F>
 __device__ __forceinline__ void for_window(F f)
 {
+    static_assert(RW >= 32 && RW <= 64, "window width");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int ly = warp; ly < RH; ly += NWARP) {
-#pragma unroll
-        for (int lx0 = 0; lx0 < RW; lx0 += 32) {
-            const int lx = lx0 + lane;
-            if (lx < RW) f(ly, lx);
+    for (int ly = warp; ly < RH; ly += NWARP) f(ly, lane);
+    if constexpr (RW > 32) {
+        constexpr int TW = RW - 32, NT = RH * TW;
+        const int t0 = (threadIdx.x + T2THREADS - (RH % NWARP) * 32) % T2THREADS;
+        for (int t = t0; t < NT; t += T2THREADS) {
+            const int ly = t / TW;
+            f(ly, 32 + (t - ly * TW));
         }
     }
 }
-
 // Lattice-weighted (D2Q9) isotropic operators on a window of row width RW.
 // The Laplacian sums neighbour differences (f_i - f_0), which are exact or
 // nearly so for a smooth field, so mu = 4a phi(phi^2-1) - kappa Lap(phi) keeps
@@ -193,12 +197,12 @@ __global__ void __launch_bounds__(T2THREADS)
         const long long off = R.off;
         const T *gr = in.f[F_R] + off, *gu = in.f[F_U] + off, *gv = in.f[F_V] + off;
         T *dr_ = stage0 + b * STAGE, *du = dr_ + A2, *dv = du + A2, *dp = dv + A2;
-        // window columns of this lane (halo 2: rho', u, v; halo 4: phi)
+        // window column of this lane in the first 32 columns (halo 2: rho',
+        // u, v; halo 4: phi); the packed columns beyond wrap per element
         const int c2a = wrap_or_clamp(x0 - 2 + lane, nx, perx);
-        const int c2b = wrap_or_clamp(x0 - 2 + lane + 32, nx, perx);
         for_window<RW2, RH2>([&](int ly, int lx) {
             const long long row = (long long)wrap_or_clamp(y0 - 2 + ly, ny, pery) * nx;
-            const long long k = row + (lx < 32 ? c2a : c2b);
+            const long long k = row + (lx < 32 ? c2a : wrap_or_clamp(x0 - 2 + lx, nx, perx));
             const int i = ly * RW2 + lx;
             cp_async_elem(dr_ + i, gr + k);
             cp_async_elem(du + i, gu + k);
@@ -207,10 +211,10 @@ __global__ void __launch_bounds__(T2THREADS)
         if (TP) {
             const T *gp = in.f[F_PHI] + off;
             const int c4a = wrap_or_clamp(x0 - 4 + lane, nx, perx);
-            const int c4b = wrap_or_clamp(x0 - 4 + lane + 32, nx, perx);
             for_window<RW4, RH4>([&](int ly, int lx) {
                 const long long row = (long long)wrap_or_clamp(y0 - 4 + ly, ny, pery) * nx;
-                cp_async_elem(dp + ly * RW4 + lx, gp + row + (lx < 32 ? c4a : c4b));
+                cp_async_elem(dp + ly * RW4 + lx,
+                              gp + row + (lx < 32 ? c4a : wrap_or_clamp(x0 - 4 + lx, nx, perx)));
             });
         }
     };
