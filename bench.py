@@ -184,6 +184,34 @@ def cpu_baseline(seconds: float = 12.0):
                       f"{steps1} steps in {dt1:.1f} s; FP64 C oracle"}
 
 
+def oracle_jobs_rate(jobs, seconds: float, threads: int):
+    """Time the CPU oracle as it stands on independent problems: ``jobs`` is a
+    list of (params, [rho, u, v, w, phi]) (w, phi may be None); thread i steps
+    jobs i, i + T, ... one step each in turn until ``seconds`` have passed.
+    Returns (node updates per second, node updates done, wall seconds)."""
+    from concurrent.futures import ThreadPoolExecutor
+    from oracle import c_oracle as co
+    co.step(jobs[0][0], *[f.copy() if f is not None else None for f in jobs[0][1]], nsteps=1)
+
+    def nodes(p):
+        return p.nx * p.ny * p.nz
+
+    t0 = time.perf_counter()
+
+    def worker(mine):
+        done = 0
+        while time.perf_counter() - t0 < seconds:
+            for p, f in mine:
+                co.step(p, *f, nsteps=1)
+                done += nodes(p)
+        return done
+
+    with ThreadPoolExecutor(threads) as ex:
+        total = sum(ex.map(worker, [jobs[i::threads] for i in range(threads)]))
+    dt = time.perf_counter() - t0
+    return total / dt, total, dt
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -289,6 +317,20 @@ def run_batched_drops(args):
         errs_u.append(float(np.linalg.norm(g32[1] - g64[1]) / den))
     for h in singles:
         h.close()
+    cpu = None
+    if not args.no_cpu_baseline:
+        from oracle import c_oracle as co
+        threads = host_threads()
+        jobs = []
+        for r, st in list(zip(runs, states))[:2 * threads]:
+            p = co.make_params((r.n, r.n), nu=r.nu, two_phase=True, sigma=r.sigma, W=r.W, M=r.M)
+            jobs.append((p, [st[0].copy(), st[1].copy(), st[2].copy(), None, st[3].copy()]))
+        rate, done, secs = oracle_jobs_rate(jobs, 12.0, threads)
+        cpu = {"value": rate / 1e9, "unit": "GLUPS", "cores": threads, "kind": "oracle",
+               "sample": f"the first {len(jobs)} runs of the same seeded batch "
+                         f"({sum(r.n * r.n for r in runs[:len(jobs)])} nodes), FP64 C oracle, "
+                         f"one step per run in turn, {threads} threads each owning a subset "
+                         f"of the runs: {done:.3g} node updates in {secs:.1f} s"}
     bytes_per_lu = 32  # rho', u, v, phi read and written, 4 B each
     per_launch = ms32 / 1e3 / args.steps
     peak, peak_kind = measured_peaks()
@@ -313,6 +355,7 @@ def run_batched_drops(args):
                          "sampled_runs": len(errs_phi)},
         "mass_nonfinite": float(np.sum(red[:, 7])),
         "clocks": clk.summary(),
+        "cpu_baseline": cpu,
     }))
     batch.close()
     return 0
@@ -662,6 +705,16 @@ def run_cavity(args):
     f64, f32 = fields["fp64"], fields["fp32"]
     rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
     out["fp32_vs_fp64"] = {"u_rel_l2": rel(f32[1], f64[1]), "v_rel_l2": rel(f32[2], f64[2])}
+    if not args.no_cpu_baseline:
+        from oracle import c_oracle as co
+        threads = host_threads()
+        p = co.make_params((n, n), nu=nu, bc=[1, 1, 1, 2, 0, 0], lid_u=(lid, 0, 0))
+        jobs = [(p, [rho.copy(), u.copy(), v.copy(), None, None]) for _ in range(threads)]
+        rate, done, secs = oracle_jobs_rate(jobs, 12.0, threads)
+        out["cpu_baseline"] = {
+            "value": rate / 1e9, "unit": "GLUPS", "cores": threads, "kind": "oracle",
+            "sample": f"{threads} independent copies of the 1024^2 cavity from rest, one per "
+                      f"thread, FP64 C oracle: {done:.3g} node updates in {secs:.1f} s"}
     c = n // 2
     out["centreline"] = {"u_min_vertical": float(f64[1][:, c].min()) / lid,
                          "v_max_horizontal": float(f64[2][c, :].max()) / lid,
