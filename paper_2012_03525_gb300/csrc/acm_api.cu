@@ -277,8 +277,11 @@ void release(acm_handle *h)
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     for (void *p : h->scratch)
         if (p) cudaFree(p);
-    for (cudaStream_t st : h->side) cudaStreamDestroy(st);
-    for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+    // a creation that failed part-way leaves null entries
+    for (cudaStream_t st : h->side)
+        if (st) cudaStreamDestroy(st);
+    for (cudaEvent_t e : h->ev)
+        if (e) cudaEventDestroy(e);
 }
 
 bool field_used(const acm_handle *h, int f)
