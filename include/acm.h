@@ -169,7 +169,7 @@ acm_status acm_fields(acm_handle *h, int run, double *rho, double *u, double *v,
  *   out[8*r + 5] = max over nodes of | |u^n| - |u^{n-1}| | (change made by
  *                  the last step; 0 before the first step)
  *   out[8*r + 6] = max |u|
- *   out[8*r + 7] = number of non-finite values among rho and u
+ *   out[8*r + 7] = number of nodes holding a non-finite value of rho or u
  * OUT is a host array of 8 * acm_nruns(h) doubles.  Deterministic: the
  * summation order does not depend on timing.  Synchronous. */
 acm_status acm_reduce_mass(acm_handle *h, double *out);

@@ -808,3 +808,109 @@ def test_c_and_numpy_oracles_agree(oracle_lib, shape, two_phase):
         assert np.abs(st[1 + a] - v2[a]).max() < 1e-15
     if two_phase:
         assert np.abs(ph - ph2).max() < 1e-14
+
+
+# ---------------------------------------------------------------- diagnostics
+# oracle_reduce (the FP64 integral diagnostics of Section 3: E_k of the
+# Taylor-Green test, the steady-state criterion of the cavity test) against
+# discrete sums fixed by trigonometry on whole periods: sum_j cos^2(2 pi j/N)
+# = N/2 and sum_j sin(2 pi j/N) = 0 for N >= 3.
+
+def test_reduce_kinetic_energy_tgv_closed_form(oracle_lib):
+    """2D TGV on whole periods: 1/2 sum |u|^2 = u0^2 N^2 / 4 exactly (a
+    missing 1/2 doubles it, a dropped component halves it); sum rho u =
+    sum rho v = 0; max |u| = u0, reached at (x, y) = (0, N/4)."""
+    co = oracle_lib
+    n, u0 = 48, 0.037
+    rho, u, v = wl.tgv2d(n, u0)
+    out = co.reduce(co.make_params((n, n)), rho, u, v)
+    assert out[4] == pytest.approx(u0 ** 2 * n ** 2 / 4, rel=1e-13)
+    assert abs(out[1]) < 1e-15 * n * n and abs(out[2]) < 1e-15 * n * n
+    assert out[6] == pytest.approx(u0, rel=1e-15)
+    assert out[5] == 0.0 and out[7] == 0.0
+
+
+def test_reduce_mass_and_momentum_closed_form(oracle_lib):
+    """rho = 1 + a cos^2(kx), u = U + b sin(ky), v = V + c sin(ky) with
+    rho' = a cos^2 not correlated with u: sum rho = N^2 (1 + a/2) and
+    sum rho u = N^2 U (1 + a/2) + 0 -- then rho = 1 + a sin(ky) correlated
+    with u: sum rho u = N^2 (U + a b / 2) (a dropped rho factor gives
+    N^2 U)."""
+    co = oracle_lib
+    n, a, b, c, U, V = 40, 0.03, 0.02, -0.05, 0.011, -0.007
+    k = 2 * math.pi / n
+    y, x = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    p = co.make_params((n, n))
+    u = U + b * np.sin(k * y)
+    v = V + c * np.sin(k * y)
+    out = co.reduce(p, 1 + a * np.cos(k * x) ** 2, u, v)
+    assert out[0] == pytest.approx(n * n * (1 + a / 2), rel=1e-14)
+    assert out[1] == pytest.approx(n * n * U * (1 + a / 2), rel=1e-12)
+    out = co.reduce(p, 1 + a * np.sin(k * y), u, v)
+    assert out[0] == pytest.approx(n * n, rel=1e-14)
+    assert out[1] == pytest.approx(n * n * (U + a * b / 2), rel=1e-12)
+    assert out[2] == pytest.approx(n * n * (V + a * c / 2), rel=1e-12)
+    assert out[3] == 0.0
+
+
+def test_reduce_3d_components_closed_form(oracle_lib):
+    """3D: u = A cos(kx), v = B cos(ky), w = C cos(kz) with distinct A, B, C:
+    E_k = N^3 (A^2 + B^2 + C^2) / 4 (a dropped or repeated component
+    fails); rho = 1 + a sin(kz), w' = W + C cos(kz) + d sin(kz):
+    sum rho w' = N^3 (W + a d / 2)."""
+    co = oracle_lib
+    n, A, B, C = 12, 0.01, 0.02, 0.04
+    k = 2 * math.pi / n
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    u, v, w = A * np.cos(k * x), B * np.cos(k * y), C * np.cos(k * z)
+    p = co.make_params((n, n, n))
+    out = co.reduce(p, np.ones((n, n, n)), u, v, w)
+    assert out[4] == pytest.approx(n ** 3 * (A * A + B * B + C * C) / 4, rel=1e-13)
+    a, d, W = 0.02, 0.03, 0.005
+    w2 = W + C * np.cos(k * z) + d * np.sin(k * z)
+    out = co.reduce(p, 1 + a * np.sin(k * z), u, v, w2)
+    assert out[3] == pytest.approx(n ** 3 * (W + a * d / 2), rel=1e-12)
+    assert abs(out[1]) < 1e-15 * n ** 3 and abs(out[2]) < 1e-15 * n ** 3
+
+
+def test_reduce_maxima_at_first_and_last_node(oracle_lib):
+    """max | |u| - |u_prev| | and max |u| planted at the first and the last
+    node (an off-by-one loop bound misses one of them); a node whose
+    velocity turns without changing its magnitude contributes 0 (the
+    criterion is on |u|, not on |u - u_prev|)."""
+    co = oracle_lib
+    shape = (7, 9)
+    rng = np.random.default_rng(3)
+    u = 0.01 * rng.uniform(-1, 1, shape)
+    v = 0.01 * rng.uniform(-1, 1, shape)
+    up, vp = u.copy(), v.copy()
+    # first node: |u| grows by exactly 0.004 (3-4-5 triangles)
+    up[0, 0], vp[0, 0] = 0.003, 0.004            # |u_prev| = 0.005
+    u[0, 0], v[0, 0] = 0.0054, 0.0072            # |u| = 0.009
+    # a node turned by 90 degrees at |u| = 0.02: |u - u_prev| = 0.028 > 0.004
+    up[3, 4], vp[3, 4] = 0.02, 0.0
+    u[3, 4], v[3, 4] = 0.0, 0.02
+    # last node: the largest speed
+    u[-1, -1], v[-1, -1] = -0.03, 0.04           # |u| = 0.05
+    up[-1, -1], vp[-1, -1] = -0.03, 0.04
+    out = co.reduce(co.make_params(shape), np.ones(shape), u, v, prev=(up, vp))
+    assert out[5] == pytest.approx(0.004, rel=1e-12)
+    assert out[6] == pytest.approx(0.05, rel=1e-15)
+
+
+def test_reduce_counts_nonfinite_nodes(oracle_lib):
+    """Three bad nodes holding four non-finite values (NaN in rho; +inf in
+    v; NaN in u and -inf in w at one node): out[7] counts nodes, 3."""
+    co = oracle_lib
+    shape = (4, 5, 6)
+    rho, u, v, w = np.ones(shape), np.zeros(shape), np.zeros(shape), np.zeros(shape)
+    rho[0, 0, 0] = np.nan
+    v[1, 2, 3] = np.inf
+    u[3, 4, 5] = np.nan
+    w[3, 4, 5] = -np.inf
+    with np.errstate(invalid="ignore"):
+        out = co.reduce(co.make_params(shape), rho, u, v, w)
+    assert out[7] == 3.0
+    z = np.zeros(shape)
+    clean = co.reduce(co.make_params(shape), np.ones(shape), z, z, z)
+    assert clean[7] == 0.0 and clean[0] == 120.0
