@@ -117,6 +117,54 @@ enum { ACM_SCHEME_SMAMES = 0, ACM_SCHEME_MAMES = 1 };
  * acm_set_fields. */
 acm_status acm_create(const acm_params *params, acm_handle **out);
 
+/* Elements of the precision's type (double for ACM_FP64, float for
+ * ACM_FP32_DEV) in ONE field buffer of a single-grid solver for PARAMS: the
+ * storage acm_create_ext expects per field and buffer.  2D storage is the
+ * grid itself ([y][x], unpadded); 3D storage is padded by two ghost layers
+ * in x and y ([z][ny + 4][px], px = nx + 4 rounded up to a multiple of 8).
+ * Host-only: needs no GPU.  ACM_EINVAL for invalid parameters. */
+acm_status acm_storage_elems(const acm_params *params, size_t *elems);
+
+/* Like acm_create, but the field storage is device memory the CALLER owns
+ * (e.g. tensors of a framework's caching allocator), and the handle runs on
+ * the caller's stream:
+ *   dev_fields  10 device pointers, buffer-major: dev_fields[5 b + f] is
+ *               field f of time-level buffer b (b = 0, 1; f = 0 rho - rho0,
+ *               1 u, 2 v, 3 w, 4 phi).  Each holds acm_storage_elems(params)
+ *               elements and starts on a 256-byte boundary (the 3D step
+ *               stages planes by TMA).  Entries of fields the run does not
+ *               have (w in 2D, phi in single-phase runs) must be NULL; the
+ *               ten buffers must not overlap.
+ *   stream      cudaStream_t every call of the handle uses (NULL = legacy
+ *               default stream); the handle creates no stream of its own.
+ * The library zero-fills the buffers at creation (on STREAM), never frees
+ * them (acm_destroy leaves them to the caller, who must keep them alive
+ * until then) and allocates only its small bookkeeping arrays (run
+ * descriptor, error word, reduction partials, one host-transfer staging
+ * field).  After acm_set_fields and acm_step, buffer acm_current_buffer(h)
+ * holds the state in the storage layout above.  Scratch fields of the 3D
+ * two-phase step are still allocated by the library.  ACM_EINVAL for a
+ * missing, misaligned or superfluous pointer. */
+acm_status acm_create_ext(const acm_params *params, void *const *dev_fields, void *stream,
+                          acm_handle **out);
+
+/* Index (0 or 1) of the buffer holding the current state. */
+int acm_current_buffer(const acm_handle *h);
+
+/* Stability pre-check (not in the paper, which reports blow-ups of
+ * under-resolved runs in Sections 3.1 and 3.3).  A von Neumann analysis of
+ * the forward-Euler step with centred advection and diffusion (the velocity
+ * equation of Eq. 2.11 linearised about a uniform flow u) gives two
+ * necessary conditions: |u|^2 dt <= 2 nu and 2 dim nu dt <= 1 (delta_x = 1).
+ * *ratio receives max(max_nodes |u|^2 dt / (2 nu), 2 dim nu dt) over the N
+ * nodes of the host arrays u, v, w (w may be NULL in 2D): a value above 1
+ * means the run is expected to blow up.  acm_set_fields applies the same
+ * check to every run's initial velocity and, when the ratio exceeds 1,
+ * still returns ACM_OK but leaves a warning in acm_last_error.  Host-only:
+ * needs no GPU. */
+acm_status acm_stability_ratio(const acm_params *params, const double *u, const double *v,
+                               const double *w, size_t n, double *ratio);
+
 /* Create a solver for NRUNS grids (a batch).
  * dim 2: independent runs.  params[r] describes run r; all runs share
  *   precision and two_phase.  Grid sizes and physical parameters may differ
@@ -173,6 +221,40 @@ acm_status acm_fields(acm_handle *h, int run, double *rho, double *u, double *v,
  * OUT is a host array of 8 * acm_nruns(h) doubles.  Deterministic: the
  * summation order does not depend on timing.  Synchronous. */
 acm_status acm_reduce_mass(acm_handle *h, double *out);
+
+/* Velocity error of run RUN against a reference field (Eq. 3.2 of Section
+ * 3.1, written there for u of the Taylor-Green vortex):
+ *   out[a] = sqrt( sum (u_a - u_a,ref)^2 / sum u_a,ref^2 ),  a = 0, 1, 2,
+ * summed over every node in FP64 on the GPU.  u_ref, v_ref, w_ref are host
+ * arrays like acm_set_fields' (a NULL reference gives out[a] = 0; w_ref is
+ * ignored in 2D).  A zero reference norm gives the absolute root-sum-square
+ * error.  Synchronous. */
+acm_status acm_reduce_error(acm_handle *h, int run, const double *u_ref, const double *v_ref,
+                            const double *w_ref, double *out);
+
+/* Laplace-law diagnostics of every run of a two-phase handle (FP64 on the
+ * GPU), from phi and mu = 4 a phi (phi^2 - 1) - kappa Lap_iso(phi) of
+ * Section 2 (Eq. 2.14's chemical potential, same isotropic Laplacian as the
+ * step; wall nodes, whose Laplacian needs the wall's ghost values, are left
+ * out):
+ *   out[8 r + 0] = A = sum (1 + phi)/2: area (2D) or volume (3D) of the
+ *                  phi > 0 phase
+ *   out[8 r + 1] = R_eff = sqrt(A / pi) (2D) or (3 A / (4 pi))^(1/3) (3D)
+ *   out[8 r + 2] = mu_G = sum mu (1 - phi^2) / sum (1 - phi^2), mu weighted
+ *                  by the interface profile: for a tanh interface it is the
+ *                  curvature term of mu, (dim - 1) sigma / (2 R), and at
+ *                  equilibrium the uniform mu_0
+ *   out[8 r + 3] = mean mu over nodes with phi > 0.95 (inside the drop)
+ *   out[8 r + 4] = mean mu over nodes with phi < -0.95 (outside)
+ *   out[8 r + 5] = p_in - p_out, p = c_s^2 rho averaged over the same sets
+ *   out[8 r + 6] = the Laplace law's mu_0 = (dim - 1) sigma / (2 R_eff)
+ *                  (2D: sigma / (2R), 3D: sigma / R; the jump of
+ *                  p + phi mu - a (phi^2 - 1)^2 across the interface is
+ *                  2 mu_0)
+ *   out[8 r + 7] = number of nodes with phi > 0.95
+ * Means over an empty set are 0.  ACM_EINVAL for single-phase handles.
+ * Synchronous. */
+acm_status acm_reduce_laplace(acm_handle *h, double *out);
 
 /* Launch tuning knobs (the autotuner of the Python layer sweeps them).
  * Changing a knob drops captured graphs.  Returns ACM_EINVAL for an unknown
@@ -283,7 +365,11 @@ const char *acm_closure_last_error(const acm_closure *c);
  *   dim, nx, ny, nz  grid (nz = 1 in 2D); fields are contiguous [z][y][x],
  *                    x fastest, unpadded
  *   precision        ACM_FP64 (double arrays) or ACM_FP32_DEV (float arrays)
- *   rho              ABSOLUTE density (device pointer)
+ *   rho0             reference density: the rho array holds rho - rho0 (the
+ *                    deviation form the solver stores, which keeps the
+ *                    O(Ma^2) density signal's digits in FP32); pass 0 for an
+ *                    array of absolute density
+ *   rho              density minus rho0 (device pointer)
  *   u, v, w          velocity (device pointers; w ignored in 2D)
  *   u_prev..w_prev   velocity before the last step for out[5], or all NULL
  *                    (then out[5] = 0)
@@ -298,10 +384,12 @@ const char *acm_closure_last_error(const acm_closure *c);
  * scratch and keeps the last call's contents: each call rewrites every
  * partial it later reads, so nothing needs clearing, but calls that overlap
  * on the GPU (different streams, no ordering between them) race on it and
- * must be serialised by the caller.  The call is asynchronous; errors found
- * on the host return before anything is enqueued.  Message of the last
+ * must be serialised by the caller.  The call is asynchronous: it enqueues
+ * three kernels on STREAM (the descriptor is written by a kernel from its
+ * launch argument) and does not wait for the stream; errors found on the
+ * host return before anything is enqueued.  Message of the last
  * failure on the calling thread: acm_noalloc_last_error(). */
-acm_status acm_reduce_mass_noalloc(int dim, int nx, int ny, int nz, int precision,
+acm_status acm_reduce_mass_noalloc(int dim, int nx, int ny, int nz, int precision, double rho0,
                                    const void *rho, const void *u, const void *v, const void *w,
                                    const void *u_prev, const void *v_prev, const void *w_prev,
                                    int blocks, double *out_dev, void *stream);

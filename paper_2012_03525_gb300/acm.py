@@ -27,7 +27,9 @@ EXPORTS = ["acm_create", "acm_batch_create", "acm_set_stream", "acm_nruns", "acm
            "acm_closure_forward", "acm_closure_loss_grad", "acm_closure_train_step",
            "acm_closure_gather", "acm_closure_apply", "acm_closure_destroy",
            "acm_closure_last_error", "acm_reduce_mass_noalloc",
-           "acm_noalloc_last_error"]
+           "acm_noalloc_last_error", "acm_storage_elems", "acm_create_ext",
+           "acm_current_buffer", "acm_stability_ratio", "acm_reduce_error",
+           "acm_reduce_laplace"]
 
 
 class AcmError(RuntimeError):
@@ -81,10 +83,18 @@ def load():
         "acm_autotune": ([H, ctypes.c_int, dp], ctypes.c_int),
         "acm_destroy": ([H], ctypes.c_int),
         "acm_last_error": ([H], ctypes.c_char_p),
-        "acm_reduce_mass_noalloc": ([ctypes.c_int] * 5 + [ctypes.c_void_p] * 7 +
+        "acm_reduce_mass_noalloc": ([ctypes.c_int] * 5 + [ctypes.c_double] +
+                                    [ctypes.c_void_p] * 7 +
                                     [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p],
                                     ctypes.c_int),
         "acm_noalloc_last_error": ([], ctypes.c_char_p),
+        "acm_storage_elems": ([P, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+        "acm_create_ext": ([P, ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p,
+                            ctypes.POINTER(H)], ctypes.c_int),
+        "acm_current_buffer": ([H], ctypes.c_int),
+        "acm_stability_ratio": ([P, dp, dp, dp, ctypes.c_size_t, dp], ctypes.c_int),
+        "acm_reduce_error": ([H, ctypes.c_int, dp, dp, dp, dp], ctypes.c_int),
+        "acm_reduce_laplace": ([H, dp], ctypes.c_int),
         "acm_restrict": ([H, H, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_void_p,
                           ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
         "acm_closure_num_params": ([], ctypes.c_size_t),
@@ -164,28 +174,58 @@ def _dptr(a):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
+def storage_elems(params: Params) -> int:
+    """acm_storage_elems: elements per field buffer of a single-grid solver."""
+    lib = load()
+    n = ctypes.c_size_t(0)
+    st = lib.acm_storage_elems(ctypes.byref(params), ctypes.byref(n))
+    if st != OK:
+        raise AcmError(st, lib.acm_last_error(None).decode())
+    return n.value
+
+
+def stability_ratio(params: Params, u, v, w=None) -> float:
+    """acm_stability_ratio on host velocity arrays (> 1: expected to blow up)."""
+    lib = load()
+    r = ctypes.c_double(0.0)
+    st = lib.acm_stability_ratio(ctypes.byref(params), _dptr(np.ascontiguousarray(u, np.float64)),
+                                 _dptr(np.ascontiguousarray(v, np.float64)),
+                                 None if w is None else _dptr(np.ascontiguousarray(w, np.float64)),
+                                 int(np.asarray(u).size), ctypes.byref(r))
+    if st != OK:
+        raise AcmError(st, lib.acm_last_error(None).decode())
+    return r.value
+
+
 def reduce_mass_noalloc(dim, nx, ny, nz, precision, rho, u, v, w, prev, blocks, out_dev,
-                        stream=0):
+                        stream=0, rho0=0.0):
     """acm_reduce_mass_noalloc on caller-owned device buffers (raw device
-    addresses as ints; ``prev`` = (u_prev, v_prev, w_prev) addresses or None).
-    Raises AcmError on a non-zero status."""
+    addresses as ints; ``prev`` = (u_prev, v_prev, w_prev) addresses or None;
+    ``rho`` holds rho - rho0).  Raises AcmError on a non-zero status."""
     lib = load()
     pu, pv, pw = prev if prev is not None else (None, None, None)
-    st = lib.acm_reduce_mass_noalloc(dim, nx, ny, nz, precision, rho, u, v, w, pu, pv, pw,
-                                     blocks, out_dev, stream)
+    st = lib.acm_reduce_mass_noalloc(dim, nx, ny, nz, precision, float(rho0), rho, u, v, w,
+                                     pu, pv, pw, blocks, out_dev, stream)
     if st != OK:
         raise AcmError(st, lib.acm_noalloc_last_error().decode())
 
 
 class Solver:
     """One handle: a single grid (``Solver(params)``) or a batch
-    (``Solver([params, ...])``)."""
+    (``Solver([params, ...])``).  ``ext_fields`` (10 device addresses,
+    buffer-major, None for absent fields) and ``stream`` select
+    acm_create_ext: the field storage then belongs to the caller."""
 
-    def __init__(self, params):
+    def __init__(self, params, ext_fields=None, stream=0):
         lib = load()
         self._lib = lib
         self._h = ctypes.c_void_p()
-        if isinstance(params, (list, tuple)):
+        if ext_fields is not None:
+            arr = (ctypes.c_void_p * 10)(*[0 if a is None else a for a in ext_fields])
+            st = lib.acm_create_ext(ctypes.byref(params), arr, ctypes.c_void_p(stream),
+                                    ctypes.byref(self._h))
+            self.params = [params]
+        elif isinstance(params, (list, tuple)):
             arr = (Params * len(params))(*params)
             st = lib.acm_batch_create(arr, len(params), ctypes.byref(self._h))
             self.params = list(params)
@@ -261,6 +301,29 @@ class Solver:
         out = np.zeros(8 * self.nruns)
         self._check(self._lib.acm_reduce_mass(self._h, _dptr(out)))
         return out.reshape(self.nruns, 8) if self.nruns > 1 else out
+
+    def reduce_error(self, u_ref, v_ref, w_ref=None, run=0):
+        """Eq. (3.2) relative L2 error of each velocity component against the
+        host reference fields (acm_reduce_error); 0 for a None reference."""
+        out = np.zeros(3)
+        refs = [None if a is None else np.ascontiguousarray(a, np.float64)
+                for a in (u_ref, v_ref, w_ref)]
+        self._check(self._lib.acm_reduce_error(self._h, run, *[_dptr(a) for a in refs],
+                                               _dptr(out)))
+        return out
+
+    def reduce_laplace(self):
+        """acm_reduce_laplace: per run [A, R_eff, mu_G, mu_in, mu_out,
+        p_in - p_out, (dim - 1) sigma / (2 R_eff), n_in]."""
+        out = np.zeros(8 * self.nruns)
+        self._check(self._lib.acm_reduce_laplace(self._h, _dptr(out)))
+        return out.reshape(self.nruns, 8) if self.nruns > 1 else out
+
+    def current_buffer(self):
+        return self._lib.acm_current_buffer(self._h)
+
+    def last_error(self):
+        return self._lib.acm_last_error(self._h).decode()
 
     def restrict_to(self, coarse=None, factor=4, out_dev=None, scales=(1.0, 1.0), u_scale=None,
                     rho_scale=None):

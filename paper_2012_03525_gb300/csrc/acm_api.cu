@@ -42,6 +42,7 @@ struct acm_handle {
     int64_t scanned_steps = 0;  // step count at the last non-finite scan (3D)
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    bool own_fields = true;           // false: acm_create_ext (caller-owned buffers)
     unsigned *derr = nullptr;
     unsigned sticky = 0;
     double *dpartials = nullptr;
@@ -265,9 +266,10 @@ void drop_graph(acm_handle *h)
 void release(acm_handle *h)
 {
     drop_graph(h);
-    for (int b = 0; b < 2; ++b)
-        for (int f = 0; f < NFIELD; ++f)
-            if (h->buf[b][f]) cudaFree(h->buf[b][f]);
+    if (h->own_fields)
+        for (int b = 0; b < 2; ++b)
+            for (int f = 0; f < NFIELD; ++f)
+                if (h->buf[b][f]) cudaFree(h->buf[b][f]);
     if (h->druns) cudaFree(h->druns);
     if (h->dwork) cudaFree(h->dwork);
     if (h->derr) cudaFree(h->derr);
@@ -291,7 +293,17 @@ bool field_used(const acm_handle *h, int f)
     return true;
 }
 
-acm_status create_common(const acm_params *params, int nruns, acm_handle **out)
+// elements per field pool of a run described by d (each run starts on a
+// 32-element, i.e. 128/256-byte, boundary)
+size_t run_elems(const RunDesc &d)
+{
+    const size_t n = (size_t)d.px * d.py * (d.nz + 2 * d.zg);
+    return (n + 31) / 32 * 32;
+}
+
+// ext != nullptr: acm_create_ext (10 caller-owned buffers, caller's stream)
+acm_status create_common(const acm_params *params, int nruns, acm_handle **out,
+                         void *const *ext = nullptr, cudaStream_t ext_stream = nullptr)
 {
     if (out) *out = nullptr;
     if (!params || !out || nruns < 1) return fail(nullptr, ACM_EINVAL, "null argument or nruns < 1");
@@ -353,8 +365,7 @@ acm_status create_common(const acm_params *params, int nruns, acm_handle **out)
     for (int r = 0; r < nruns; ++r) {
         RunDesc d = describe(params[r]);
         d.off = (long long)off;
-        const size_t n = (size_t)d.px * d.py * (d.nz + 2 * d.zg);
-        off += (n + 31) / 32 * 32;
+        off += run_elems(d);
         if (d.zg) h->halo = true;
         h->runs.push_back(d);
         const long long np = (long long)d.nx * d.ny * d.nz;
@@ -384,20 +395,37 @@ acm_status create_common(const acm_params *params, int nruns, acm_handle **out)
         }                                            \
     } while (0)
 
-    CKB(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
-    h->own_stream = true;
+    if (ext) {
+        h->stream = ext_stream;
+        h->own_stream = false;
+    } else {
+        CKB(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+        h->own_stream = true;
+    }
     if (h->halo && nruns > 1) {
         h->side.assign(nruns - 1, nullptr);
         h->ev.assign(nruns, nullptr);
         for (auto &st : h->side) CKB(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
         for (auto &e : h->ev) CKB(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     }
-    for (int b = 0; b < 2; ++b)
-        for (int f = 0; f < NFIELD; ++f)
-            if (field_used(h, f)) {
-                CKB(cudaMalloc(&h->buf[b][f], h->pool * h->esize()));
-                CKB(cudaMemset(h->buf[b][f], 0, h->pool * h->esize()));
-            }
+    if (ext) {
+        // caller-owned storage: checked by acm_create_ext, zero-filled here
+        h->own_fields = false;
+        for (int b = 0; b < 2; ++b)
+            for (int f = 0; f < NFIELD; ++f)
+                if (field_used(h, f)) {
+                    h->buf[b][f] = ext[NFIELD * b + f];
+                    CKB(cudaMemsetAsync(h->buf[b][f], 0, h->pool * h->esize(), h->stream));
+                }
+        CKB(cudaStreamSynchronize(h->stream));
+    } else {
+        for (int b = 0; b < 2; ++b)
+            for (int f = 0; f < NFIELD; ++f)
+                if (field_used(h, f)) {
+                    CKB(cudaMalloc(&h->buf[b][f], h->pool * h->esize()));
+                    CKB(cudaMemset(h->buf[b][f], 0, h->pool * h->esize()));
+                }
+    }
     if (h->dim == 3 && h->two_phase)
         for (void *&p : h->scratch) {
             CKB(cudaMalloc(&p, h->pool * h->esize()));
@@ -414,7 +442,10 @@ acm_status create_common(const acm_params *params, int nruns, acm_handle **out)
     const long long per_run_blocks = (maxn + 255) / 256;
     h->red_blocks = (int)std::max<long long>(
         1, std::min<long long>(per_run_blocks, nruns == 1 ? 4LL * h->sms : 16LL));
-    CKB(cudaMalloc(&h->dpartials, sizeof(double) * 8 * (size_t)h->red_blocks * nruns));
+    // room for the partials of every reduction: 8 (acm_reduce_mass), 2 per
+    // block (acm_reduce_error) or LAPLACE_PARTIALS (acm_reduce_laplace)
+    CKB(cudaMalloc(&h->dpartials,
+                   sizeof(double) * LAPLACE_PARTIALS * (size_t)h->red_blocks * nruns));
     CKB(cudaMalloc(&h->dout, sizeof(double) * 8 * nruns));
     CKB(cudaMalloc(&h->dstage, sizeof(double) * (size_t)maxn));
     if (build_maps(h) != ACM_OK) return bail(ACM_ECUDA);
@@ -633,6 +664,59 @@ acm_status acm_batch_create(const acm_params *params, int nruns, acm_handle **ou
     return create_common(params, nruns, out);
 }
 
+acm_status acm_storage_elems(const acm_params *params, size_t *elems)
+{
+    if (!params || !elems) return fail(nullptr, ACM_EINVAL, "null argument");
+    std::string why;
+    if (validate(*params, why) != ACM_OK) return fail(nullptr, ACM_EINVAL, why);
+    *elems = run_elems(describe(*params));
+    return ACM_OK;
+}
+
+acm_status acm_create_ext(const acm_params *params, void *const *dev_fields, void *stream,
+                          acm_handle **out)
+{
+    if (out) *out = nullptr;
+    if (!params || !dev_fields || !out) return fail(nullptr, ACM_EINVAL, "null argument");
+    std::string why;
+    if (validate(*params, why) != ACM_OK) return fail(nullptr, ACM_EINVAL, why);
+    const bool used[NFIELD] = {true, true, true, params->dim == 3, params->two_phase != 0};
+    for (int b = 0; b < 2; ++b)
+        for (int f = 0; f < NFIELD; ++f) {
+            const void *p = dev_fields[NFIELD * b + f];
+            if (used[f] && !p)
+                return fail(nullptr, ACM_EINVAL, "missing device buffer for a field the run has");
+            if (!used[f] && p)
+                return fail(nullptr, ACM_EINVAL,
+                            "device buffer given for a field the run does not have");
+            if (p && (reinterpret_cast<uintptr_t>(p) & 255))
+                return fail(nullptr, ACM_EINVAL, "device buffers must start on 256-byte boundaries");
+        }
+    return create_common(params, 1, out, dev_fields, static_cast<cudaStream_t>(stream));
+}
+
+int acm_current_buffer(const acm_handle *h) { return h ? h->cur : -1; }
+
+acm_status acm_stability_ratio(const acm_params *params, const double *u, const double *v,
+                               const double *w, size_t n, double *ratio)
+{
+    if (!params || !u || !v || !ratio || (params->dim == 3 && !w))
+        return fail(nullptr, ACM_EINVAL, "null argument");
+    if (!(params->dt > 0) || !(params->nu >= 0) || (params->dim != 2 && params->dim != 3))
+        return fail(nullptr, ACM_EINVAL, "bad dim, dt or nu");
+    double q = 0.0;
+    for (size_t i = 0; i < n; ++i) {
+        double s = u[i] * u[i] + v[i] * v[i];
+        if (params->dim == 3) s += w[i] * w[i];
+        if (!(s <= q)) q = s;  // NaN propagates
+    }
+    const double nu = params->nu, dt = params->dt;
+    const double adv = nu > 0 ? q * dt / (2.0 * nu) : (q > 0 || std::isnan(q) ? INFINITY : 0.0);
+    const double dif = 2.0 * params->dim * nu * dt;
+    *ratio = std::isnan(adv) ? adv : std::max(adv, dif);
+    return ACM_OK;
+}
+
 acm_status acm_set_stream(acm_handle *h, void *stream)
 {
     if (!h) return fail(nullptr, ACM_EINVAL, "null handle");
@@ -841,6 +925,17 @@ acm_status acm_set_fields(acm_handle *h, int run, const double *rho, const doubl
     h->steps = 0;
     h->scanned_steps = 0;
     h->have_fields[run] = 1;
+    // stability pre-check of the initial velocity: a warning, not an error
+    double ratio = 0.0;
+    h->err.clear();
+    if (acm_stability_ratio(&h->params[run], u, v, w, n, &ratio) == ACM_OK && !(ratio <= 1.0)) {
+        char msg[256];
+        std::snprintf(msg, sizeof msg,
+                      "warning: run %d is expected to be unstable: max(|u|^2 dt / (2 nu), "
+                      "2 dim nu dt) = %.3g > 1 on the initial field",
+                      run, ratio);
+        h->err = msg;
+    }
     return ACM_OK;
 }
 
@@ -934,6 +1029,61 @@ acm_status acm_reduce_mass(acm_handle *h, double *out)
                                  pw, h->dpartials, h->red_blocks, h->dout, h->stream);
     }
     if (e != cudaSuccess) return cuda_fail(h, e, "reduction kernels");
+    CK(h, cudaMemcpyAsync(out, h->dout, sizeof(double) * 8 * h->nruns, cudaMemcpyDeviceToHost,
+                          h->stream));
+    return check_flags(h);
+}
+
+acm_status acm_reduce_error(acm_handle *h, int run, const double *u_ref, const double *v_ref,
+                            const double *w_ref, double *out)
+{
+    NvtxRange nvtx_("acm_reduce_error");
+    if (!h || !out) return fail(h, ACM_EINVAL, "null argument");
+    if (run < 0 || run >= h->nruns) return fail(h, ACM_EINVAL, "run index out of range");
+    CK(h, cudaSetDevice(h->device));
+    const RunDesc &R = h->runs[run];
+    const size_t n = (size_t)h->npoints[run];
+    const double *refs[3] = {u_ref, v_ref, h->dim == 3 ? w_ref : nullptr};
+    double res[3] = {0.0, 0.0, 0.0};
+    for (int a = 0; a < 3; ++a) {
+        if (!refs[a]) continue;
+        CK(h, cudaMemcpyAsync(h->dstage, refs[a], n * sizeof(double), cudaMemcpyHostToDevice,
+                              h->stream));
+        cudaError_t e =
+            h->prec == ACM_FP64
+                ? launch_error_l2<double>(R, static_cast<const double *>(h->buf[h->cur][F_U + a]),
+                                          h->dstage, h->dpartials, h->red_blocks, h->dout + a,
+                                          h->stream)
+                : launch_error_l2<float>(R, static_cast<const float *>(h->buf[h->cur][F_U + a]),
+                                         h->dstage, h->dpartials, h->red_blocks, h->dout + a,
+                                         h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "error kernels");
+        // the staging buffer is reused by the next component
+        CK(h, cudaMemcpyAsync(&res[a], h->dout + a, sizeof(double), cudaMemcpyDeviceToHost,
+                              h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+    }
+    for (int a = 0; a < 3; ++a) out[a] = res[a];
+    return check_flags(h);
+}
+
+acm_status acm_reduce_laplace(acm_handle *h, double *out)
+{
+    NvtxRange nvtx_("acm_reduce_laplace");
+    if (!h || !out) return fail(h, ACM_EINVAL, "null argument");
+    if (!h->two_phase) return fail(h, ACM_EINVAL, "Laplace diagnostics need a two-phase handle");
+    CK(h, cudaSetDevice(h->device));
+    cudaError_t e =
+        h->prec == ACM_FP64
+            ? launch_laplace<double>(h->druns, h->nruns, h->dim,
+                                     static_cast<const double *>(h->buf[h->cur][F_PHI]),
+                                     static_cast<const double *>(h->buf[h->cur][F_R]),
+                                     h->dpartials, h->red_blocks, h->dout, h->stream)
+            : launch_laplace<float>(h->druns, h->nruns, h->dim,
+                                    static_cast<const float *>(h->buf[h->cur][F_PHI]),
+                                    static_cast<const float *>(h->buf[h->cur][F_R]),
+                                    h->dpartials, h->red_blocks, h->dout, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "Laplace kernels");
     CK(h, cudaMemcpyAsync(out, h->dout, sizeof(double) * 8 * h->nruns, cudaMemcpyDeviceToHost,
                           h->stream));
     return check_flags(h);

@@ -130,6 +130,17 @@ template <typename T>
 cudaError_t launch_halo(const RunDesc *druns, int nruns, long long plane, Fields<T> f,
                         cudaStream_t s);
 
+// Eq. (3.2) error sums of one field against an unpadded reference, and the
+// Laplace-law diagnostics of two-phase runs (acm_diag.cu); partials hold 2
+// (error) or 9 x nruns (Laplace) doubles per block.
+constexpr int LAPLACE_PARTIALS = 9;
+template <typename T>
+cudaError_t launch_error_l2(const RunDesc &R, const T *f, const double *ref, double *partials,
+                            int blocks, double *out, cudaStream_t s);
+template <typename T>
+cudaError_t launch_laplace(const RunDesc *druns, int nruns, int dim, const T *phi, const T *rho,
+                           double *partials, int blocks, double *out, cudaStream_t s);
+
 template <typename T>
 cudaError_t launch_scan_nonfinite(const T *a, const T *b, long long n, unsigned *err,
                                   cudaStream_t s);

@@ -11,6 +11,7 @@
 // of memory the library would otherwise cudaMalloc.  Those arrays exist on
 // every GPU that loads the library, until the process exits.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -33,6 +34,11 @@ acm::RunDesc *g_run_dev[MAX_DEVICES];
 std::mutex g_setup_mutex;
 thread_local std::string g_noalloc_err;
 
+// writes the run descriptor from a kernel argument: the launch copies the
+// argument by value, so the call neither reads pageable host memory
+// asynchronously nor waits for the stream
+__global__ void k_set_run(acm::RunDesc R) { g_run = R; }
+
 acm_status noalloc_fail(acm_status st, const std::string &msg)
 {
     g_noalloc_err = msg;
@@ -44,7 +50,8 @@ acm_status noalloc_fail(acm_status st, const std::string &msg)
 extern "C" const char *acm_noalloc_last_error(void) { return g_noalloc_err.c_str(); }
 
 extern "C" acm_status acm_reduce_mass_noalloc(int dim, int nx, int ny, int nz, int precision,
-                                              const void *rho, const void *u, const void *v,
+                                              double rho0, const void *rho, const void *u,
+                                              const void *v,
                                               const void *w, const void *u_prev,
                                               const void *v_prev, const void *w_prev, int blocks,
                                               double *out_dev, void *stream)
@@ -54,6 +61,7 @@ extern "C" acm_status acm_reduce_mass_noalloc(int dim, int nx, int ny, int nz, i
         return noalloc_fail(ACM_EINVAL, "grid sizes must be >= 1 (nz = 1 in 2D)");
     if (precision != ACM_FP64 && precision != ACM_FP32_DEV)
         return noalloc_fail(ACM_EINVAL, "bad precision");
+    if (!std::isfinite(rho0)) return noalloc_fail(ACM_EINVAL, "rho0 must be finite");
     if (!rho || !u || !v || (dim == 3 && !w) || !out_dev)
         return noalloc_fail(ACM_EINVAL, "missing field or output pointer");
     if ((u_prev || v_prev || w_prev) && (!u_prev || !v_prev || (dim == 3 && !w_prev)))
@@ -87,7 +95,7 @@ extern "C" acm_status acm_reduce_mass_noalloc(int dim, int nx, int ny, int nz, i
     }
 
     // the run descriptor of the existing reduction kernels: an unpadded grid
-    // holding absolute density (rho0 = 0)
+    // holding rho - rho0
     acm::RunDesc R;
     std::memset(&R, 0, sizeof(R));
     R.nx = nx;
@@ -97,9 +105,10 @@ extern "C" acm_status acm_reduce_mass_noalloc(int dim, int nx, int ny, int nz, i
     R.py = ny;
     R.pad = 0;
     R.off = 0;
-    R.rho0 = 0.0;
+    R.rho0 = rho0;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    e = cudaMemcpyAsync(g_run_dev[dev], &R, sizeof(R), cudaMemcpyHostToDevice, s);
+    k_set_run<<<1, 1, 0, s>>>(R);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return noalloc_fail(ACM_ECUDA, cudaGetErrorString(e));
 
     if (precision == ACM_FP64) {

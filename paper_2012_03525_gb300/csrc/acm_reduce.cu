@@ -25,39 +25,61 @@ __device__ __forceinline__ long long storage_index(const RunDesc &R, int dim, lo
     return R.off + ((z + R.zg) * R.py + y + R.pad) * R.px + x + R.pad;
 }
 
+// Pass 1 walks rows of contiguous nodes: in 3D the x-rows of the padded
+// storage (row = (z, y), one 32-bit division per row), in 2D chunks of
+// RCHUNK consecutive nodes of the unpadded run.  Blocks take rows
+// blockIdx.x, blockIdx.x + gridDim.x, ...; threads stride along the row.
+// No per-node index arithmetic beyond one add, so the kernel is bound by
+// its FP64 arithmetic (narrow on GB300), not by integer division.  max |u|
+// is taken over |u|^2 and square-rooted once per block.
+constexpr int RCHUNK = 4 * RT;
+
 template <typename T>
 __global__ void __launch_bounds__(RT)
     k_reduce(const RunDesc *__restrict__ runs, int dim, Fields<T> cur, const T *pu, const T *pv,
              const T *pw, double *partials)
 {
     const RunDesc &R = runs[blockIdx.y];
-    const long long n = (long long)R.nx * R.ny * R.nz;
+    const long long n2 = (long long)R.nx * R.ny;
+    const int nrow = dim == 3 ? R.ny * R.nz : (int)((n2 + RCHUNK - 1) / RCHUNK);
     double s[5] = {0, 0, 0, 0, 0};
-    double mdu = 0.0, mu = 0.0, nbad = 0.0;
+    double mdu = 0.0, mq = 0.0, nbad = 0.0;
     const double rho0 = R.rho0;
-    for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < n;
-         i += (long long)gridDim.x * RT) {
-        const long long k = storage_index(R, dim, i);
-        const double r = (double)cur.f[F_R][k];
-        const double u = (double)cur.f[F_U][k];
-        const double v = (double)cur.f[F_V][k];
-        const double w = dim == 3 ? (double)cur.f[F_W][k] : 0.0;
-        const double rho = rho0 + r;
-        s[0] += r;
-        s[1] += rho * u;
-        s[2] += rho * v;
-        s[3] += rho * w;
-        const double q = u * u + v * v + w * w;
-        s[4] += 0.5 * q;
-        const double sp = sqrt(q);
-        mu = fmax(mu, sp);
-        if (pu) {
-            const double a = (double)pu[k], b = (double)pv[k], c = dim == 3 ? (double)pw[k] : 0.0;
-            mdu = fmax(mdu, fabs(sp - sqrt(a * a + b * b + c * c)));
+    const T *fr = cur.f[F_R], *fu = cur.f[F_U], *fv = cur.f[F_V], *fw = cur.f[F_W];
+    for (int row = blockIdx.x; row < nrow; row += gridDim.x) {
+        long long base;
+        int len;
+        if (dim == 3) {
+            const int z = row / R.ny, y = row - z * R.ny;
+            base = R.off + ((long long)(z + R.zg) * R.py + y + R.pad) * R.px + R.pad;
+            len = R.nx;
+        } else {
+            base = R.off + (long long)row * RCHUNK;
+            len = (int)min((long long)RCHUNK, n2 - (long long)row * RCHUNK);
         }
-        nbad += (!isfinite(r) || !isfinite(u) || !isfinite(v) || !isfinite(w)) ? 1.0 : 0.0;
+        for (int x = threadIdx.x; x < len; x += RT) {
+            const long long k = base + x;
+            const double r = (double)fr[k];
+            const double u = (double)fu[k];
+            const double v = (double)fv[k];
+            const double w = dim == 3 ? (double)fw[k] : 0.0;
+            const double rho = rho0 + r;
+            s[0] += r;
+            s[1] += rho * u;
+            s[2] += rho * v;
+            s[3] += rho * w;
+            const double q = u * u + v * v + w * w;
+            s[4] += q;
+            mq = fmax(mq, q);
+            if (pu) {
+                const double a = (double)pu[k], b = (double)pv[k];
+                const double c = dim == 3 ? (double)pw[k] : 0.0;
+                mdu = fmax(mdu, fabs(sqrt(q) - sqrt(a * a + b * b + c * c)));
+            }
+            nbad += (!isfinite(r) || !isfinite(u) || !isfinite(v) || !isfinite(w)) ? 1.0 : 0.0;
+        }
     }
-    double vals[8] = {s[0], s[1], s[2], s[3], s[4], mdu, mu, nbad};
+    double vals[8] = {s[0], s[1], s[2], s[3], 0.5 * s[4], mdu, sqrt(mq), nbad};
     __shared__ double red[8][RT / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll

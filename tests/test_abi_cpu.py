@@ -2,9 +2,11 @@
 include/acm.h declares, and rejects invalid parameters before touching a GPU.
 No compute call is made here."""
 import ctypes
+import math
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_2012_03525_gb300 import acm, build
@@ -116,3 +118,41 @@ def test_subdomain_params_split():
     assert all(q.bc[4] == q.bc[5] == acm.BC_HALO for q in p)
     with pytest.raises(ValueError):
         acm.subdomain_params((10, 6, 8), (3, 6))
+
+
+# ---------------------------------------------------------------- host-only calls
+def test_storage_elems_layouts(lib):
+    """2D storage is the grid itself; 3D is padded by two ghost layers in x
+    and y, rows rounded up to 8 elements; each rounded to 32 elements."""
+    assert acm.storage_elems(acm.make_params((64, 64))) == 4096
+    assert acm.storage_elems(acm.make_params((5, 7))) == 64          # 35 -> 64
+    nz, ny, nx = 10, 12, 30
+    px = ((nx + 4 + 7) // 8) * 8
+    n = px * (ny + 4) * nz
+    assert acm.storage_elems(acm.make_params((nz, ny, nx))) == (n + 31) // 32 * 32
+    with pytest.raises(acm.AcmError):
+        acm.storage_elems(acm.make_params((8, 8), dt=0.0))
+
+
+def test_stability_ratio_von_neumann(lib):
+    """max(|u|^2 dt / (2 nu), 2 dim nu dt): forward Euler with centred
+    advection and diffusion.  The decaying-turbulence set-up of the learned
+    closure (u_max ~ 0.15, nu = 5e-4) is unstable at dt = 1 and stable at
+    dt = 1/30; the 256^3 Taylor-Green case (u0 = 0.05, Re = 1600) is just
+    inside; a diffusion number above 1/(2 dim) is caught as well."""
+    u = np.array([0.1, -0.15, 0.02])
+    v = np.array([0.0, 0.0, 0.05])
+    p = acm.make_params((1, 3), dt=1.0, nu=5e-4)
+    assert acm.stability_ratio(p, u, v) == pytest.approx(0.15 ** 2 / (2 * 5e-4))
+    p = acm.make_params((1, 3), dt=1.0 / 30, nu=5e-4)
+    assert acm.stability_ratio(p, u, v) == pytest.approx(0.15 ** 2 / 30 / (2 * 5e-4))
+    assert acm.stability_ratio(p, u, v) < 1
+    nu = 0.05 * (256 / (2 * math.pi)) / 1600
+    p = acm.make_params((1, 1, 1), nu=nu)
+    r = acm.stability_ratio(p, np.array([0.05]), np.array([0.0]), np.array([0.0]))
+    assert 0.9 < r < 1.0
+    p = acm.make_params((1, 1, 1), nu=0.2)  # 2 * 3 * 0.2 = 1.2
+    assert acm.stability_ratio(p, np.zeros(1), np.zeros(1), np.zeros(1)) == pytest.approx(1.2)
+    p = acm.make_params((1, 2), nu=0.0)
+    assert acm.stability_ratio(p, np.array([0.0, 1e-3]), np.zeros(2)) == math.inf
+    assert acm.stability_ratio(p, np.zeros(2), np.zeros(2)) == 0.0

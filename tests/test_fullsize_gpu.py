@@ -90,7 +90,8 @@ def test_tgv256_fp64_two_steps_whole_grid(oracle_lib):
         s.set_fields(*state)
         s.step(2)
         got = list(s.fields())
-    # w starts at zero and is O(1e-5) after two steps, so velocity errors are
-    # measured against 1 % of u0 per node (a floor of 5e-4): at 1e-12 that
-    # is ~5e-16 per node, two ulp of u0
-    assert_parity([rho, u, v, w, None], got, vscale=0.01 * U0)
+    # w starts at zero and is O(1e-5) after two steps, below the oracle's own
+    # rounding of the pressure term (absolute rho ~ 1 differenced: ~2e-17 per
+    # step), so velocity errors are measured against 1 % of u0 per node (a
+    # floor of 5e-4): at 1e-12 that is ~5e-16 per node, two ulp of u0
+    assert_parity([rho, u, v, w, None], got, vfloor=0.01 * U0)

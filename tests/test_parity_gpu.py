@@ -69,26 +69,27 @@ def run_both(oracle_lib, shape, state, nsteps, gpu_kw=None, **kw):
     return ref, got
 
 
-def assert_parity(ref, got, rho0=1.0, tol=TOL64, tol_rho=None, vscale=1e-6):
+def assert_parity(ref, got, rho0=1.0, tol=TOL64, tol_rho=None, vfloor=None):
     """Per-field relative L2.  Density: the paper's variable is the absolute
     rho (compared at ``tol``); its deviation rho - rho0 is compared at
     ``tol_rho`` -- for FP64 1e-9, because the oracle stores absolute rho, whose
-    rounding (1.1e-16 per step) is ~3e-13 of a 3e-4 deviation per step."""
+    rounding (1.1e-16 per step) is ~3e-13 of a 3e-4 deviation per step.
+    Velocities are measured against their own norm, with a per-node floor
+    ``vfloor`` (default min(1e-6, 1 % of the largest velocity)) that only
+    matters for a component that is (nearly) zero everywhere; a floor above
+    1 % of the largest velocity is refused."""
     tol_rho = (1e-9 if tol <= TOL64 else tol) if tol_rho is None else tol_rho
     if tol <= TOL64:
         assert rel_l2(got[0], ref[0]) <= tol
     assert rel_l2(got[0] - rho0, ref[0] - rho0) <= tol_rho, rel_l2(got[0] - rho0, ref[0] - rho0)
+    vmax = max(float(np.abs(ref[k]).max()) for k in (1, 2, 3) if ref[k] is not None)
+    vfloor = min(1e-6, 0.01 * vmax) if vfloor is None else vfloor
+    assert vfloor <= 0.01 * vmax
     for k in (1, 2, 3, 4):
         if ref[k] is not None and np.abs(ref[k]).max() > 0:
             err = rel_l2(got[k], ref[k])
             if k < 4:
-                # velocities are measured against a floor ``vscale``: 1e-6 by
-                # default (Ma < 2e-6), the capillary velocity sigma/(rho0 nu)
-                # (Section 3.4) for two-phase runs, whose velocities are the
-                # small residual of nearly cancelling pressure and
-                # surface-tension forces and carry their ~1e-16 absolute
-                # rounding per step
-                floor = vscale * math.sqrt(ref[k].size)
+                floor = vfloor * math.sqrt(ref[k].size)
                 err = float(np.sqrt(((got[k] - ref[k]) ** 2).sum()) /
                             max(np.sqrt((ref[k] ** 2).sum()), floor))
             assert err <= tol, (k, err)
@@ -244,7 +245,7 @@ def test_two_phase_drop_fp64(oracle_lib, shape):
     u = u + 0.002 * _smooth(rng, shape)
     ref, got = run_both(oracle_lib, shape, [rho, u, v, phi], 120, nu=0.1, two_phase=True,
                         sigma=1e-2, W=4.0, M=0.3)
-    assert_parity(ref, got, vscale=1e-2 / 0.1)
+    assert_parity(ref, got)
 
 
 def test_two_phase_drop_fp32(oracle_lib):
@@ -269,6 +270,10 @@ def test_batched_two_phase_runs_match_oracle_each(oracle_lib):
         params.append(acm.make_params((n, n), nu=0.1, two_phase=True, sigma=sigma, W=4.0, M=0.1))
         states.append(wl.drop2d(n, R, 4.0, eps=eps))
     steps = 80
+    rng = np.random.default_rng(12)
+    for st in states:   # a smooth flow through each drop: every term acts
+        st[1] = st[1] + 2e-3 * _smooth(rng, st[1].shape)
+        st[2] = st[2] + 2e-3 * _smooth(rng, st[2].shape)
     with acm.Solver(params) as s:
         for r, st in enumerate(states):
             s.set_fields(st[0], st[1], st[2], None, st[3], run=r)
@@ -280,7 +285,7 @@ def test_batched_two_phase_runs_match_oracle_each(oracle_lib):
             p = co.make_params((n, n), nu=0.1, two_phase=True, sigma=sigma, W=4.0, M=0.1)
             co.step(p, rho, u, v, None, phi, nsteps=steps)
             try:
-                assert_parity([rho, u, v, None, phi], got, vscale=sigma / 0.1)
+                assert_parity([rho, u, v, None, phi], got)
             except AssertionError as e:
                 failures.append((r, n, sigma, str(e)[:200],
                                  float(np.abs(u).max()), float(np.abs(got[1] - u).max())))

@@ -53,7 +53,7 @@ def test_two_phase_3d_fp64(oracle_lib, shape, bc, theta):
     sigma, nu = 1e-2, 0.1
     ref, got = run_both(oracle_lib, shape, st, 60, nu=nu, bc=bc, two_phase=True, sigma=sigma,
                         W=4.0, M=0.3, theta_deg=theta, g=(0.0, 0.0, -1e-6))
-    assert_parity(ref, got, vscale=sigma / nu)
+    assert_parity(ref, got)
 
 
 def test_two_phase_3d_fp32(oracle_lib):
