@@ -97,6 +97,12 @@ typedef struct {
                            corrector of Eqs. (2.6)-(2.9) that it replaces
                            (comparison scheme: 2D, periodic, single-phase,
                            no body force; sat_mask is ignored) */
+    double rho_ratio;   /* two-phase: 0 = the body force acts on both phases
+                           (+ dt rho^{n+1} g); r > 0 = Boussinesq drop force
+                           of Section 3.5 for a drop/ambient density ratio r:
+                           the force acts on the drop (phi = +1) phase only,
+                           scaled by 2 (r - 1)/(r + 1), i.e.
+                           + dt rho^{n+1} g 2 (r - 1)/(r + 1) (1 + phi^n)/2 */
 } acm_params;
 
 /* time-stepping scheme */
@@ -219,7 +225,12 @@ acm_status acm_fields(acm_handle *h, int run, double *rho, double *u, double *v,
  *   out[8*r + 6] = max |u|
  *   out[8*r + 7] = number of nodes holding a non-finite value of rho or u
  * OUT is a host array of 8 * acm_nruns(h) doubles.  Deterministic: the
- * summation order does not depend on timing.  Synchronous. */
+ * summation order does not depend on timing.  FP64 storage: every operation
+ * in FP64.  FP32 storage: per node FP32 arithmetic only (GB300's FP64 pipe
+ * is narrow), with compensated FP32 sums carrying ~48 significant bits and
+ * the products rho' u_a added exactly, combined in FP64 per thread; out[5]
+ * has ~1e-7 relative precision (FP32 denominator |u| + |u_prev|).
+ * Synchronous. */
 acm_status acm_reduce_mass(acm_handle *h, double *out);
 
 /* Velocity error of run RUN against a reference field (Eq. 3.2 of Section

@@ -58,6 +58,8 @@ typedef struct {
     double sigma, W, M;    /* surface tension, interface width, mobility */
     int sat_mask;          /* bit0: continuity SAT, bit1: momentum SAT */
     double theta_deg;      /* contact angle of wall faces (two-phase) */
+    double rho_ratio;      /* two-phase: 0 = body force on both phases; r > 0 =
+                              Boussinesq drop force (Section 3.5) */
 } oracle_params;
 
 typedef struct {
@@ -368,7 +370,16 @@ int oracle_step(const oracle_params *p, double *rho, double *u, double *v,
                         if (sat_m)
                             mn -= (p->nu + 0.5 * cs2 * dt) *
                                   (dcen(rho1, &nb, a) - dcen(rho, &nb, a));
-                        mn += dt * rho1[c0] * p->g[a];
+                        /* body force; with the Boussinesq approximation of
+                           Section 3.5 it acts on the drop only, times
+                           (rho_L - rho_G) / ((rho_L + rho_G)/2) =
+                           2 (r - 1)/(r + 1), the drop's share of a node
+                           being its volume fraction (1 + phi)/2 */
+                        double ga = p->g[a];
+                        if (p->two_phase && p->rho_ratio > 0.0)
+                            ga *= 2.0 * (p->rho_ratio - 1.0) / (p->rho_ratio + 1.0) *
+                                  (0.5 * (1.0 + phi[c0]));
+                        mn += dt * rho1[c0] * ga;
                         if (p->two_phase)
                             mn += dt * (-phi[c0] * grad_iso(&G, mu, F_MIRROR, i, j, k, a));
                         mnew[a][c0] = mn;

@@ -33,6 +33,7 @@ class OracleParams(ctypes.Structure):
         ("sigma", ctypes.c_double), ("W", ctypes.c_double), ("M", ctypes.c_double),
         ("sat_mask", ctypes.c_int),
         ("theta_deg", ctypes.c_double),
+        ("rho_ratio", ctypes.c_double),
     ]
 
 
@@ -72,7 +73,7 @@ def _load():
 
 def make_params(shape, dt=1.0, nu=0.01, rho0=1.0, bc=None, lid_u=(0, 0, 0), g=(0, 0, 0),
                 two_phase=False, sigma=0.0, W=4.0, M=0.0, sat_mask=3,
-                theta_deg=90.0) -> OracleParams:
+                theta_deg=90.0, rho_ratio=0.0) -> OracleParams:
     """``shape`` is (ny, nx) for 2D or (nz, ny, nx) for 3D (array order)."""
     p = OracleParams()
     if len(shape) == 2:
@@ -90,6 +91,7 @@ def make_params(shape, dt=1.0, nu=0.01, rho0=1.0, bc=None, lid_u=(0, 0, 0), g=(0
     p.sigma, p.W, p.M = sigma, W, M
     p.sat_mask = sat_mask
     p.theta_deg = theta_deg
+    p.rho_ratio = rho_ratio
     return p
 
 

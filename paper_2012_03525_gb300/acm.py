@@ -49,6 +49,7 @@ class Params(ctypes.Structure):
         ("precision", ctypes.c_int), ("sat_mask", ctypes.c_int),
         ("theta_deg", ctypes.c_double),
         ("scheme", ctypes.c_int),
+        ("rho_ratio", ctypes.c_double),
     ]
 
 
@@ -127,7 +128,7 @@ def load():
 
 def make_params(shape, dt=1.0, nu=0.01, rho0=1.0, bc=None, lid_u=(0, 0, 0), g=(0, 0, 0),
                 two_phase=False, sigma=0.0, W=4.0, M=0.0, precision=FP64, sat_mask=3,
-                theta_deg=90.0, scheme=SCHEME_SMAMES) -> Params:
+                theta_deg=90.0, scheme=SCHEME_SMAMES, rho_ratio=0.0) -> Params:
     """``shape`` is (ny, nx) for 2D or (nz, ny, nx) for 3D (array order)."""
     p = Params()
     if len(shape) == 2:
@@ -147,6 +148,7 @@ def make_params(shape, dt=1.0, nu=0.01, rho0=1.0, bc=None, lid_u=(0, 0, 0), g=(0
     p.sat_mask = sat_mask
     p.theta_deg = theta_deg
     p.scheme = scheme
+    p.rho_ratio = rho_ratio
     return p
 
 

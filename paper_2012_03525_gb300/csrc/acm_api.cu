@@ -144,6 +144,8 @@ acm_status validate(const acm_params &p, std::string &why)
         if (!(p.W > 0) || !(p.sigma >= 0) || !(p.M >= 0)) return bad("bad sigma/W/M");
         if (!std::isfinite(p.theta_deg)) return bad("non-finite contact angle");
     }
+    if (!std::isfinite(p.rho_ratio) || p.rho_ratio < 0) return bad("rho_ratio must be >= 0");
+    if (p.rho_ratio > 0 && !p.two_phase) return bad("rho_ratio needs a two-phase run");
     for (int d = 0; d < 3; ++d)
         if (!std::isfinite(p.g[d]) || !std::isfinite(p.lid_u[d])) return bad("non-finite g/lid");
     return ACM_OK;
@@ -189,6 +191,14 @@ RunDesc describe(const acm_params &p)
     c[C_KAPPA] = r.kappa;
     c[C_M] = r.M;
     c[C_WET] = 2.0 * (2.0 / p.W) * std::cos(p.theta_deg * 3.14159265358979323846 / 180.0);
+    if (p.two_phase && p.rho_ratio > 0) {
+        const double beta = 2.0 * (p.rho_ratio - 1.0) / (p.rho_ratio + 1.0);
+        c[C_BQA] = 0.5 * beta;
+        c[C_BQB] = 0.5 * beta;
+    } else {
+        c[C_BQA] = 1.0;
+        c[C_BQB] = 0.0;
+    }
     for (int k = 0; k < NCOEF; ++k) {
         r.cd[k] = c[k];
         r.cf[k] = (float)c[k];

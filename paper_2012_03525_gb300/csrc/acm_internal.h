@@ -34,6 +34,8 @@ enum {
     C_GX, C_GY, C_GZ, C_LIDX, C_LIDY, C_LIDZ,
     C_A, C_KAPPA, C_M,
     C_WET,    // 2 (2/W) cos(theta): wetting term of the ghost order parameter
+    C_BQA, C_BQB,  // body-force factor A + B phi^n: (1, 0), or the Boussinesq
+                   // drop force (Section 3.5) beta/2 (1 + phi), beta = 2 (r-1)/(r+1)
     NCOEF
 };
 

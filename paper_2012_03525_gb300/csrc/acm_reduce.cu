@@ -29,23 +29,13 @@ __device__ __forceinline__ long long storage_index(const RunDesc &R, int dim, lo
 // storage (row = (z, y), one 32-bit division per row), in 2D chunks of
 // RCHUNK consecutive nodes of the unpadded run.  Blocks take rows
 // blockIdx.x, blockIdx.x + gridDim.x, ...; threads stride along the row.
-// No per-node index arithmetic beyond one add, so the kernel is bound by
-// its FP64 arithmetic (narrow on GB300), not by integer division.  max |u|
-// is taken over |u|^2 and square-rooted once per block.
 constexpr int RCHUNK = 4 * RT;
 
-template <typename T>
-__global__ void __launch_bounds__(RT)
-    k_reduce(const RunDesc *__restrict__ runs, int dim, Fields<T> cur, const T *pu, const T *pv,
-             const T *pw, double *partials)
+template <typename F>
+__device__ __forceinline__ void for_rows(const RunDesc &R, int dim, F &&node)
 {
-    const RunDesc &R = runs[blockIdx.y];
     const long long n2 = (long long)R.nx * R.ny;
     const int nrow = dim == 3 ? R.ny * R.nz : (int)((n2 + RCHUNK - 1) / RCHUNK);
-    double s[5] = {0, 0, 0, 0, 0};
-    double mdu = 0.0, mq = 0.0, nbad = 0.0;
-    const double rho0 = R.rho0;
-    const T *fr = cur.f[F_R], *fu = cur.f[F_U], *fv = cur.f[F_V], *fw = cur.f[F_W];
     for (int row = blockIdx.x; row < nrow; row += gridDim.x) {
         long long base;
         int len;
@@ -57,29 +47,126 @@ __global__ void __launch_bounds__(RT)
             base = R.off + (long long)row * RCHUNK;
             len = (int)min((long long)RCHUNK, n2 - (long long)row * RCHUNK);
         }
-        for (int x = threadIdx.x; x < len; x += RT) {
-            const long long k = base + x;
-            const double r = (double)fr[k];
-            const double u = (double)fu[k];
-            const double v = (double)fv[k];
-            const double w = dim == 3 ? (double)fw[k] : 0.0;
-            const double rho = rho0 + r;
-            s[0] += r;
-            s[1] += rho * u;
-            s[2] += rho * v;
-            s[3] += rho * w;
-            const double q = u * u + v * v + w * w;
-            s[4] += q;
-            mq = fmax(mq, q);
-            if (pu) {
-                const double a = (double)pu[k], b = (double)pv[k];
-                const double c = dim == 3 ? (double)pw[k] : 0.0;
-                mdu = fmax(mdu, fabs(sqrt(q) - sqrt(a * a + b * b + c * c)));
-            }
-            nbad += (!isfinite(r) || !isfinite(u) || !isfinite(v) || !isfinite(w)) ? 1.0 : 0.0;
-        }
+        for (int x = threadIdx.x; x < len; x += RT) node(base + x);
     }
-    double vals[8] = {s[0], s[1], s[2], s[3], 0.5 * s[4], mdu, sqrt(mq), nbad};
+}
+
+// Compensated FP32 sum (a "double-float" accumulator: s + c carries ~48
+// significant bits): Knuth's two-sum of s and x, the rounding error of the
+// addition goes into c.  Explicit round-to-nearest intrinsics keep the
+// compiler from reassociating or contracting it.
+struct CSum {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x)
+    {
+        const float t = __fadd_rn(s, x);
+        const float bp = __fsub_rn(t, s);
+        const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(x, bp));
+        c = __fadd_rn(c, err);
+        s = t;
+    }
+    // add the exact product a * b (the product's rounding error from an FMA)
+    __device__ __forceinline__ void add_prod(float a, float b)
+    {
+        const float p = __fmul_rn(a, b);
+        c = __fadd_rn(c, __fmaf_rn(a, b, -p));
+        add(p);
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+// FP64 diagnostics of FP64 storage: every operation in FP64 (the parity
+// path).  max |u| is taken over |u|^2 and square-rooted once per thread.
+__device__ __forceinline__ void reduce_node(const RunDesc &R, int dim, const double *fr,
+                                            const double *fu, const double *fv, const double *fw,
+                                            const double *pu, const double *pv, const double *pw,
+                                            long long k, double (&s)[5], double &mdu, double &mq,
+                                            double &nbad)
+{
+    const double r = fr[k], u = fu[k], v = fv[k];
+    const double w = dim == 3 ? fw[k] : 0.0;
+    const double rho = R.rho0 + r;
+    s[0] += r;
+    s[1] += rho * u;
+    s[2] += rho * v;
+    s[3] += rho * w;
+    const double q = u * u + v * v + w * w;
+    s[4] += q;
+    mq = fmax(mq, q);
+    if (pu) {
+        const double a = pu[k], b = pv[k], c = dim == 3 ? pw[k] : 0.0;
+        mdu = fmax(mdu, fabs(sqrt(q) - sqrt(a * a + b * b + c * c)));
+    }
+    nbad += (!isfinite(r) || !isfinite(u) || !isfinite(v) || !isfinite(w)) ? 1.0 : 0.0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(RT)
+    k_reduce(const RunDesc *__restrict__ runs, int dim, Fields<T> cur, const T *pu, const T *pv,
+             const T *pw, double *partials)
+{
+    const RunDesc &R = runs[blockIdx.y];
+    const T *fr = cur.f[F_R], *fu = cur.f[F_U], *fv = cur.f[F_V], *fw = cur.f[F_W];
+    double vals[8];
+    if constexpr (sizeof(T) == 8) {
+        double s[5] = {0, 0, 0, 0, 0};
+        double mdu = 0.0, mq = 0.0, nbad = 0.0;
+        for_rows(R, dim, [&](long long k) {
+            reduce_node(R, dim, fr, fu, fv, fw, pu, pv, pw, k, s, mdu, mq, nbad);
+        });
+        const double v8[8] = {s[0], s[1], s[2], s[3], 0.5 * s[4], mdu, sqrt(mq), nbad};
+        for (int q = 0; q < 8; ++q) vals[q] = v8[q];
+    } else {
+        // FP32 storage: per node only FP32 arithmetic (the FP64 pipe of GB300
+        // is narrow).  Sums are compensated; sum rho u_a = rho0 sum u_a +
+        // sum rho' u_a with the products rho' u_a added exactly; |u|^2 and
+        // the steady-state criterion | |u| - |u_prev| | =
+        // |sum_a (u_a - p_a)(u_a + p_a)| / (|u| + |u_prev|) in FP32 (relative
+        // error ~1e-7 of the value); max |u| from the argmax node's FP32
+        // components, squared and rooted in FP64.
+        CSum sr, su, sv, sw, sru, srv, srw, sq;
+        float mq = -1.f, mdu = 0.f, qu = 0.f, qv = 0.f, qw = 0.f;
+        int nbad = 0;
+        for_rows(R, dim, [&](long long k) {
+            const float r = fr[k], u = fu[k], v = fv[k];
+            const float w = dim == 3 ? fw[k] : 0.f;
+            sr.add(r);
+            su.add(u);
+            sv.add(v);
+            sw.add(w);
+            sru.add_prod(r, u);
+            srv.add_prod(r, v);
+            srw.add_prod(r, w);
+            const float q = __fmaf_rn(u, u, __fmaf_rn(v, v, __fmul_rn(w, w)));
+            sq.add(q);
+            if (q > mq) {
+                mq = q;
+                qu = u;
+                qv = v;
+                qw = w;
+            }
+            if (pu) {
+                const float a = pu[k], b = pv[k], c = dim == 3 ? pw[k] : 0.f;
+                const float dq = __fmaf_rn(__fsub_rn(u, a), __fadd_rn(u, a),
+                                           __fmaf_rn(__fsub_rn(v, b), __fadd_rn(v, b),
+                                                     __fmul_rn(__fsub_rn(w, c), __fadd_rn(w, c))));
+                const float qp = __fmaf_rn(a, a, __fmaf_rn(b, b, __fmul_rn(c, c)));
+                const float mag = __fadd_rn(sqrtf(q), sqrtf(qp));
+                if (mag > 0.f) mdu = fmaxf(mdu, fabsf(dq) / mag);
+            }
+            nbad += (!isfinite(r) || !isfinite(u) || !isfinite(v) || !isfinite(w)) ? 1 : 0;
+        });
+        const double rho0 = R.rho0;
+        const double qd = (double)qu * qu + (double)qv * qv + (double)qw * qw;
+        vals[0] = sr.value();
+        vals[1] = rho0 * su.value() + sru.value();
+        vals[2] = rho0 * sv.value() + srv.value();
+        vals[3] = rho0 * sw.value() + srw.value();
+        vals[4] = 0.5 * sq.value();
+        vals[5] = (double)mdu;
+        vals[6] = mq >= 0.f ? sqrt(qd) : 0.0;
+        vals[7] = (double)nbad;
+    }
     __shared__ double red[8][RT / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll

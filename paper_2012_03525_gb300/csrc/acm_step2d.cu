@@ -357,8 +357,14 @@ __global__ void __launch_bounds__(T2THREADS)
                 const T lmy = myE + myW + myN + myS - T(4) * my0;
                 const T ddx = T(0.5) * (sdr[c1 + 1] - sdr[c1 - 1]);
                 const T ddy = T(0.5) * (sdr[c1 + RW1] - sdr[c1 - RW1]);
-                T rhsx = -dt * fx + nudt * lmx - satm * ddx + dt * rho1 * gxb;
-                T rhsy = -dt * fy + nudt * lmy - satm * ddy + dt * rho1 * gyb;
+                T gfx = gxb, gfy = gyb;
+                if (TP) {  // body-force factor: 1, or the Boussinesq drop force
+                    const T fac = C[C_BQA] + C[C_BQB] * sphi[(ly + 4) * RW4 + (lx + 4)];
+                    gfx = gxb * fac;
+                    gfy = gyb * fac;
+                }
+                T rhsx = -dt * fx + nudt * lmx - satm * ddx + dt * rho1 * gfx;
+                T rhsy = -dt * fy + nudt * lmy - satm * ddy + dt * rho1 * gfy;
                 if (TP) {
                     const int c3 = (ly + 3) * RW3 + (lx + 3);
                     const int c4 = (ly + 4) * RW4 + (lx + 4);

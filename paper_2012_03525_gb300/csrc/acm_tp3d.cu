@@ -354,7 +354,8 @@ __global__ void __launch_bounds__(BX *BY)
             const T ddx = T(0.5) * (d[cw + 1] - d[cw - 1]);
             const T ddy = T(0.5) * (d[cw + WX] - d[cw - WX]);
             const T ddz = T(0.5) * (win(W_DR, sp)[cw] - win(W_DR, sm)[cw]);
-            const T fb = dt * rho1;
+            // body force: on both phases, or the Boussinesq drop force
+            const T fb = dt * rho1 * (C[C_BQA] + C[C_BQB] * f0);
             T rx = -dt * flux(mx) - dt * cs2 * T(0.5) * (rr[0] - rr[1]) + nudt * lap(mx, mx0) -
                    satm * ddx + fb * gfx - dt * f0 * gmx;
             T ry = -dt * flux(my) - dt * cs2 * T(0.5) * (rr[2] - rr[3]) + nudt * lap(my, my0) -

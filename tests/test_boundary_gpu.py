@@ -109,7 +109,9 @@ def test_reduce_error_tgv_matches_host_formula(prec):
     assert er[0] == pytest.approx(rel_l2(u, ue), rel=1e-12)
     assert er[1] == pytest.approx(rel_l2(v, ve), rel=1e-12)
     assert er[2] == 0.0
-    assert er[0] == pytest.approx(er[1], rel=1e-6)
+    # the symmetry of Section 3.1 holds to rounding (FP32: its 6e-8 relative
+    # rounding of u against an error of ~1e-3)
+    assert er[0] == pytest.approx(er[1], rel=1e-6 if prec == acm.FP64 else 1e-3)
     assert 1e-6 < er[0] < 2e-3
 
 

@@ -914,3 +914,24 @@ def test_reduce_counts_nonfinite_nodes(oracle_lib):
     z = np.zeros(shape)
     clean = co.reduce(co.make_params(shape), np.ones(shape), z, z, z)
     assert clean[7] == 0.0 and clean[0] == 120.0
+
+
+# ---------------------------------------------------------------- Boussinesq drop force
+@pytest.mark.parametrize("phi0,r,expect", [(1.0, 3.0, 1.0), (-1.0, 3.0, 0.0), (1.0, 1.0, 0.0),
+                                           (1.0, 1.15, 2 * 0.15 / 2.15), (0.0, 3.0, 0.5)])
+def test_boussinesq_drop_force_factor(oracle_lib, phi0, r, expect):
+    """Section 3.5: with the Boussinesq approximation the body force acts on
+    the drop only, times (rho_L - rho_G)/((rho_L + rho_G)/2) = 2 (r - 1)/(r + 1).
+    A uniform two-phase state (mu = 0, no surface tension force, no phase
+    change) then accelerates uniformly: u = n dt g 2 (r - 1)/(r + 1) (1 + phi)/2
+    -- inside the drop the full factor, outside none, at phi = 0 half."""
+    co = oracle_lib
+    shape, n, g = (6, 8), 40, 2.0 ** -12
+    rho, u, v = np.ones(shape), np.zeros(shape), np.zeros(shape)
+    phi = np.full(shape, phi0)
+    p = co.make_params(shape, nu=0.1, g=(0.0, -g, 0.0), two_phase=True, sigma=1e-2, W=4.0,
+                       M=0.1, rho_ratio=r)
+    co.step(p, rho, u, v, None, phi, nsteps=n)
+    assert np.all(u == 0.0)
+    assert np.abs(v + n * g * expect).max() <= 1e-15 * n * g
+    assert np.all(rho == 1.0)

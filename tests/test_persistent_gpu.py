@@ -15,7 +15,7 @@ import pytest
 
 from paper_2012_03525_gb300 import acm, build
 from paper_2012_03525_gb300 import workloads as wl
-from test_parity_gpu import assert_parity, _smooth
+from test_parity_gpu import assert_parity, _flow, _smooth
 
 pytestmark = pytest.mark.gpu
 
@@ -111,8 +111,7 @@ def drops(oracle_lib):
     states = []
     for r in runs:
         rho, u, v, phi = wl.drop2d(r.n, r.radius, r.W, eps=r.eps)
-        states.append([rho, u + 2e-3 * _smooth(rng, u.shape), v + 2e-3 * _smooth(rng, v.shape),
-                       phi])
+        states.append([rho, u + _flow(rng, u.shape), v + _flow(rng, v.shape), phi])
 
     def one(i):
         r = runs[i]

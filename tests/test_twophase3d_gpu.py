@@ -56,6 +56,18 @@ def test_two_phase_3d_fp64(oracle_lib, shape, bc, theta):
     assert_parity(ref, got)
 
 
+def test_two_phase_3d_boussinesq_fp64(oracle_lib):
+    """The Boussinesq drop force of Section 3.5 in 3D (z walls, gravity along
+    -z, r_rho = 1.15): parity with the oracle."""
+    shape, bc = (20, 22, 24), [0, 0, 0, 0, 1, 1]
+    phi = _drop3d(shape, 6.0, (12.0, 11.0, 12.0))
+    st = _state(shape, phi, walls=True)
+    ref, got = run_both(oracle_lib, shape, st, 60, nu=0.1, bc=bc, two_phase=True, sigma=1e-2,
+                        W=4.0, M=0.3, theta_deg=90.0, g=(0.0, 0.0, -1e-5), rho_ratio=1.15,
+                        dt=0.5)
+    assert_parity(ref, got)
+
+
 def test_two_phase_3d_fp32(oracle_lib):
     shape, bc = (17, 22, 33), [0, 0, 0, 0, 1, 1]
     phi = _drop3d(shape, 7.0, (0.0, 11.0, 16.0))

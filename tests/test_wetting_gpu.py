@@ -199,3 +199,26 @@ def test_capillary_wave_unstable_at_c5_on_gpu():
                 assert e.status == acm.EUNSTABLE
                 out[c] = False
     assert out == {5.0: False, 6.0: True}
+
+
+@pytest.mark.parametrize("prec", [acm.FP64, acm.FP32_DEV])
+def test_falling_drop_boussinesq(oracle_lib, prec):
+    """Section 3.5's falling drop in a walled 2D box (planar, not
+    axisymmetric): the body force acts on the drop only, times
+    2 (r - 1)/(r + 1) for r_rho = 1.15.  Parity with the oracle; the drop's
+    mean velocity points along g."""
+    ny, nx = 96, 40
+    rho, u, v, phi = wl.drop2d(max(nx, ny), 10.0, 4.0, cx=nx / 2 - 0.5, cy=ny - 20.0)
+    phi = np.ascontiguousarray(phi[:ny, :nx])
+    st = [np.ones((ny, nx)), np.zeros((ny, nx)), np.zeros((ny, nx)), phi]
+    kw = dict(nu=0.05, bc=[1, 1, 1, 1, 0, 0], two_phase=True, sigma=5e-3, W=4.0, M=0.2,
+              g=(0.0, -1e-4, 0.0), rho_ratio=1.15)
+    ref, got = run_both(oracle_lib, (ny, nx), st, 300, gpu_kw={"precision": prec}, **kw)
+    if prec == acm.FP64:
+        assert_parity(ref, got)
+    else:
+        assert rel_l2(got[4], ref[4]) < 1e-6
+        for k in (1, 2):
+            assert rel_l2(got[k], ref[k]) < 1e-4
+    inside = got[4] > 0
+    assert got[2][inside].mean() < 0 and abs(got[1][inside].mean()) < abs(got[2][inside].mean())
