@@ -217,7 +217,8 @@ def test_falling_drop_boussinesq(oracle_lib, prec):
     if prec == acm.FP64:
         assert_parity(ref, got)
     else:
-        assert rel_l2(got[4], ref[4]) < 1e-6
+        # FP32 velocities (relative rounding 6e-8) advect phi for 300 steps
+        assert rel_l2(got[4], ref[4]) < 5e-6
         for k in (1, 2):
             assert rel_l2(got[k], ref[k]) < 1e-4
     inside = got[4] > 0
