@@ -2,19 +2,22 @@
 // ReLU after the first two layers) that corrects a coarse-grid state
 // (rho', u, v) after solver steps, with its training on the GPU.
 //
-// All convolutions are periodic 2D cross-correlations run on the tensor
-// cores (mma.sync m16n8k16, BF16 operands, FP32 accumulation):
-//   * forward:        Y[co, p] = sum_K A[co, K] X[K, p], K = (tap, ci),
-//                     A = W in [co][tap][ci] order, X = shifted input pixels;
+// All convolutions are periodic 2D cross-correlations on the tensor cores,
+// BF16 operands and FP32 accumulation:
+//   * forward:        Y[p, co] = sum_K X[p + off(tap), ci] A[co, K], K = (tap, ci),
+//                     A = W in [co][tap][ci] order -- tcgen05.mma with the
+//                     accumulator in tensor memory (k_conv_tc);
 //   * data gradient:  dX = (W flipped, channels swapped) applied to dY -- the
 //                     same kernel with a rearranged weight matrix;
 //   * weight gradient: dW[co, (tap, ci)] = sum_p dY[co, p] X[p + off(tap), ci]
-//                     -- a GEMM whose reduction runs over pixels; per-CTA
-//                     partials are summed in a fixed order (deterministic).
+//                     -- a GEMM whose reduction runs over pixels (mma.sync
+//                     m16n8k16 fragments); per-CTA partials are summed in a
+//                     fixed order (deterministic).
 // Activations and gradients are stored as BF16 NHWC (channels contiguous),
 // the master weights, Adam moments, losses and corrections in FP32.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -58,97 +61,288 @@ __device__ __forceinline__ int wrapi(int c, int n)
 
 enum { OUT_RELU_BF16 = 0, OUT_MASK_BF16 = 1, OUT_F32_NCHW = 2 };
 
-// One 3x3 convolution layer (or its data gradient) on an 8 x 16 pixel tile.
-// x: [B][H][W][CI] bf16; A: [CO][9*CI] bf16; output by MODE (see above).
-template <int CI, int CO, int MODE>
-__global__ void __launch_bounds__(CTHREADS)
-    k_conv(const bf16 *__restrict__ x, const bf16 *__restrict__ A, const float *__restrict__ bias,
-           const bf16 *__restrict__ mask, void *__restrict__ out, int H, int W, int nout)
+// ---- 5th-generation tensor cores (tcgen05) ---------------------------------
+// One 3x3 convolution layer (or its data gradient) as per-tap GEMMs issued by
+// one thread of the CTA: for each tap (dy, dx) and 16-channel slice,
+//   D[p, co] += sum_ci X[p + (dy, dx), ci] A[co, (tap, ci)]
+// with M = the 128 pixels of an 8 x 16 tile, N = CO, K = 16, BF16 operands
+// from shared memory and the FP32 accumulator D in tensor memory (TMEM).
+// Both operands are in the no-swizzle K-major layout of 8 x 16-byte "core
+// matrices": X is staged as three copies shifted by dx (each 10 rows x 16
+// columns, periodic wrap applied while staging), so the 128 rows of the A
+// operand of tap (dy, dx) are the contiguous pixels (dy + 1) * 16 .. of copy
+// dx; the weights as [tap][ci / 8][co][8].  Persistent CTAs of 4 warps walk
+// the tiles, staging the next tile (cp.async) while the tensor cores work on
+// the current one; the epilogue reads D with tcgen05.ld (warp w holds TMEM
+// lanes 32w .. 32w + 31, i.e. tile rows 2w and 2w + 1).
+constexpr int TC_THREADS = 128;
+constexpr int TC_HP = (CTH + 2) * CTW;  // pixels of one dx-shifted halo copy
+
+template <int CI, int CO>
+struct TcGeo {
+    static constexpr int XCOPY = TC_HP * CI * 2;  // bytes of one dx copy
+    static constexpr int XBUF = 3 * XCOPY;        // one staged tile
+    static constexpr int WBYTES = 9 * CI * CO * 2;
+    static constexpr int BAR = 2 * XBUF + WBYTES;
+    static constexpr int SMEM = BAR + 16;
+    static constexpr int TCOLS = 32;              // TMEM columns (>= CO, a power of 2 >= 32)
+    static_assert(CO == 16 || CO == 32, "N of the MMA");
+    static_assert(CI % 16 == 0, "K slices of 16");
+};
+
+__device__ __forceinline__ uint32_t tc_smem(const void *p)
 {
-    constexpr int XST = CI + 8;          // smem pixel stride (bank-conflict free)
-    constexpr int K = 9 * CI, AST = K + 8;
-    constexpr int MT = CO / 16;
-    __shared__ __align__(16) bf16 xs[HALO * XST];
-    __shared__ __align__(16) bf16 as[CO * AST];
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const int g = lane >> 2, t = lane & 3;
-    const int x0 = blockIdx.x * CTW, y0 = blockIdx.y * CTH, img = blockIdx.z;
-    const bf16 *xi = x + (size_t)img * H * W * CI;
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
 
-    // weights: CO rows of K bf16 (16-byte chunks)
-    for (int i = tid; i < CO * (K / 8); i += CTHREADS) {
-        const int r = i / (K / 8), c = i - r * (K / 8);
-        *reinterpret_cast<uint4 *>(&as[r * AST + c * 8]) =
-            *reinterpret_cast<const uint4 *>(&A[(size_t)r * K + c * 8]);
+// shared-memory matrix descriptor: no swizzle, start address, leading (K)
+// and stride (M/N) byte offsets between core matrices, version 1 (sm_100)
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc,
+                                       uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc_smem(dst)), "l"(src)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool tc_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(tc_smem(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// D row of this thread (TMEM lane 32 w + lane): N FP32 columns
+template <int N>
+__device__ __forceinline__ void tc_load_row(uint32_t taddr, float (&v)[N]);
+template <>
+__device__ __forceinline__ void tc_load_row<32>(uint32_t ta, float (&v)[32])
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(ta));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+template <>
+__device__ __forceinline__ void tc_load_row<16>(uint32_t ta, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(ta));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// bounded wait: ~2^22 polls (well over a second), then give up
+constexpr int TC_WAIT_LIMIT = 1 << 22;
+
+template <int CI, int CO, int MODE>
+__global__ void __launch_bounds__(TC_THREADS)
+    k_conv_tc(const bf16 *__restrict__ x, const bf16 *__restrict__ A,
+              const float *__restrict__ bias, const bf16 *__restrict__ mask, void *__restrict__ out,
+              int H, int W, int nout, int ntiles, unsigned *err)
+{
+    using G = TcGeo<CI, CO>;
+    extern __shared__ __align__(1024) unsigned char tsm[];
+    bf16 *ws = reinterpret_cast<bf16 *>(tsm + 2 * G::XBUF);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(tsm + G::BAR);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(tsm + G::BAR + 8);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tiles_x = W / CTW, tiles_img = tiles_x * (H / CTH);
+
+    // weights [co][tap * CI + ci] -> [tap][ci / 8][co][8] (16-byte chunks)
+    for (int i = tid; i < CO * 9 * CI / 8; i += TC_THREADS) {
+        const int co = i / (9 * CI / 8), k0 = 8 * (i - co * (9 * CI / 8));
+        const int tap = k0 / CI, cc = (k0 - tap * CI) / 8;
+        *reinterpret_cast<uint4 *>(&ws[((tap * (CI / 8) + cc) * CO + co) * 8]) =
+            *reinterpret_cast<const uint4 *>(&A[(size_t)co * 9 * CI + k0]);
     }
-    // input tile with a one-pixel periodic halo
-    for (int i = tid; i < HALO * (CI / 8); i += CTHREADS) {
-        const int hp = i / (CI / 8), c = i - hp * (CI / 8);
-        const int hy = hp / (CTW + 2), hx = hp - hy * (CTW + 2);
-        const int gy = wrapi(y0 - 1 + hy, H), gx = wrapi(x0 - 1 + hx, W);
-        *reinterpret_cast<uint4 *>(&xs[hp * XST + c * 8]) =
-            *reinterpret_cast<const uint4 *>(&xi[((size_t)gy * W + gx) * CI + c * 8]);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         tc_smem(tslot)),
+                     "r"(G::TCOLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+
+    // stage tile t (periodic halo, three dx-shifted copies) into buffer b:
+    // chunk j of pixel (hr, c) of copy dx at [dx][j][hr * 16 + c][8]
+    auto stage = [&](int t, int b) {
+        const int img = t / tiles_img, r = t - img * tiles_img;
+        const int y0 = (r / tiles_x) * CTH, x0 = (r % tiles_x) * CTW;
+        const bf16 *xi = x + (size_t)img * H * W * CI;
+        unsigned char *dst = tsm + b * G::XBUF;
+        for (int i = tid; i < 3 * TC_HP * (CI / 8); i += TC_THREADS) {
+            const int j = i % (CI / 8), q = i / (CI / 8);  // channel chunk fastest: coalesced
+            const int hp = q % TC_HP, dxi = q / TC_HP;
+            const int hr = hp / CTW, c = hp - hr * CTW;
+            const int gy = wrapi(y0 - 1 + hr, H), gx = wrapi(x0 + c + dxi - 1, W);
+            cp_async16(dst + dxi * G::XCOPY + (j * TC_HP + hp) * 16,
+                       xi + ((size_t)gy * W + gx) * CI + 8 * j);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+
+    int t = blockIdx.x;
+    if (t < ntiles) stage(t, 0);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-
-    float acc[MT][2][4];
-#pragma unroll
-    for (int m = 0; m < MT; ++m)
-#pragma unroll
-        for (int j = 0; j < 2; ++j)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) acc[m][j][e] = 0.f;
-
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+    // kind::f16 instruction descriptor: D F32, A and B BF16, both K-major,
+    // N >> 3 at bit 17, M >> 4 at bit 24 (M = 128)
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(CO >> 3) << 17) |
+                           ((uint32_t)(128 >> 4) << 24);
+    uint32_t phase = 0;
+    int b = 0;
+    for (; t < ntiles; t += gridDim.x, b ^= 1) {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        // the tile's copies (generic proxy) become visible to the tensor cores
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (tid == 0) {
+            const uint32_t xb = tc_smem(tsm + b * G::XBUF), wb = tc_smem(ws);
+            int k = 0;
 #pragma unroll 1
-    for (int tap = 0; tap < 9; ++tap) {
-        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+            for (int tap = 0; tap < 9; ++tap) {
+                const int dy = tap / 3, dxi = tap % 3;  // dy + 1, dx + 1
 #pragma unroll
-        for (int cb = 0; cb < CI / 16; ++cb) {
-            const int k0 = tap * CI + cb * 16;
-            uint32_t a[MT][4];
-#pragma unroll
-            for (int m = 0; m < MT; ++m) {
-                const bf16 *ap = &as[(m * 16 + g) * AST + k0 + 2 * t];
-                a[m][0] = ld32(ap);
-                a[m][1] = ld32(ap + 8 * AST);
-                a[m][2] = ld32(ap + 8);
-                a[m][3] = ld32(ap + 8 * AST + 8);
+                for (int kc = 0; kc < CI / 16; ++kc, ++k) {
+                    const uint64_t ad = tc_desc(xb + dxi * G::XCOPY + 2 * kc * TC_HP * 16 +
+                                                    dy * CTW * 16,
+                                                TC_HP * 16, 128);
+                    const uint64_t bd = tc_desc(wb + (tap * (CI / 8) + 2 * kc) * CO * 16, CO * 16,
+                                                128);
+                    tc_mma(tmem, ad, bd, idesc, k > 0);
+                }
             }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    tc_smem(bar))
+                : "memory");
+        }
+        // stage the next tile into the other buffer while the MMAs run
+        const int tn = t + gridDim.x;
+        if (tn < ntiles) stage(tn, b ^ 1);
+        bool ok = false;
+        for (int it = 0; it < TC_WAIT_LIMIT && !ok; ++it) ok = tc_try_wait(bar, phase);
+        phase ^= 1;
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) atomicOr(err, ERR_TIMEOUT);
+            break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        float v[CO];
+        tc_load_row<CO>(tmem + ((uint32_t)(32 * warp) << 16), v);
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+
+        // epilogue: this thread's pixel p = 32 warp + lane of the tile
+        const int img = t / tiles_img, r = t - img * tiles_img;
+        const int p = 32 * warp + lane;
+        const int py = (r / tiles_x) * CTH + p / CTW, px = (r % tiles_x) * CTW + p % CTW;
+        const size_t pix = (size_t)img * H * W + (size_t)py * W + px;
+        if (MODE == OUT_F32_NCHW) {
+            float *o = static_cast<float *>(out);
 #pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                const int hp = (w + 1 + dy) * (CTW + 2) + (8 * j + g + 1 + dx);
-                const bf16 *bp = &xs[hp * XST + cb * 16 + 2 * t];
-                const uint32_t b[2] = {ld32(bp), ld32(bp + 8)};
+            for (int co = 0; co < CO; ++co)
+                if (co < nout)
+                    o[((size_t)img * nout + co) * H * W + (size_t)py * W + px] = v[co] + bias[co];
+        } else {
+            bf16 *o = static_cast<bf16 *>(out) + pix * CO;
 #pragma unroll
-                for (int m = 0; m < MT; ++m) mma_bf16(acc[m][j], a[m], b);
+            for (int c8 = 0; c8 < CO / 8; ++c8) {
+                __align__(16) bf16 h[8];
+                if (MODE == OUT_RELU_BF16) {
+#pragma unroll
+                    for (int e = 0; e < 8; ++e)
+                        h[e] = __float2bfloat16_rn(fmaxf(v[8 * c8 + e] + bias[8 * c8 + e], 0.f));
+                } else {
+                    __align__(16) bf16 mk[8];
+                    *reinterpret_cast<uint4 *>(mk) =
+                        *reinterpret_cast<const uint4 *>(mask + pix * CO + 8 * c8);
+#pragma unroll
+                    for (int e = 0; e < 8; ++e)
+                        h[e] = __float2bfloat16_rn(__bfloat162float(mk[e]) > 0.f ? v[8 * c8 + e]
+                                                                                  : 0.f);
+                }
+                *reinterpret_cast<uint4 *>(o + 8 * c8) = *reinterpret_cast<const uint4 *>(h);
             }
         }
     }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");  // no copy in flight at exit
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(G::TCOLS)
+                     : "memory");
+    }
+}
 
-    // epilogue: element e of a fragment is (co = 16m + g + 8 (e >> 1), px = 8j + 2t + (e & 1))
-#pragma unroll
-    for (int m = 0; m < MT; ++m)
-#pragma unroll
-        for (int j = 0; j < 2; ++j)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int co = m * 16 + g + 8 * (e >> 1);
-                const int px = x0 + 8 * j + 2 * t + (e & 1), py = y0 + w;
-                const size_t pix = (size_t)img * H * W + (size_t)py * W + px;
-                float vv = acc[m][j][e];
-                if (MODE == OUT_RELU_BF16) {
-                    vv = fmaxf(vv + bias[co], 0.f);
-                    static_cast<bf16 *>(out)[pix * CO + co] = __float2bfloat16_rn(vv);
-                } else if (MODE == OUT_MASK_BF16) {
-                    const float mk = __bfloat162float(mask[pix * CO + co]);
-                    static_cast<bf16 *>(out)[pix * CO + co] =
-                        __float2bfloat16_rn(mk > 0.f ? vv : 0.f);
-                } else {
-                    if (co < nout)
-                        static_cast<float *>(out)[((size_t)img * nout + co) * H * W +
-                                                  (size_t)py * W + px] = vv + bias[co];
-                }
-            }
+// persistent launch of k_conv_tc: min(tiles, SMs x resident CTAs) CTAs
+template <int CI, int CO, int MODE>
+cudaError_t conv_tc(const bf16 *x, const bf16 *A, const float *bias, const bf16 *mask, void *out,
+                    int H, int W, int nout, int batch, unsigned *err, cudaStream_t s)
+{
+    using G = TcGeo<CI, CO>;
+    static int grid_cap = 0;
+    if (grid_cap == 0) {
+        cudaError_t e = cudaFuncSetAttribute(k_conv_tc<CI, CO, MODE>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
+        if (e != cudaSuccess) return e;
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_conv_tc<CI, CO, MODE>,
+                                                          TC_THREADS, G::SMEM);
+        if (e != cudaSuccess) return e;
+        grid_cap = std::max(1, sms) * std::max(1, per);
+    }
+    const int ntiles = batch * (H / CTH) * (W / CTW);
+    const int grid = std::min(ntiles, grid_cap);
+    k_conv_tc<CI, CO, MODE><<<grid, TC_THREADS, G::SMEM, s>>>(x, A, bias, mask, out, H, W, nout,
+                                                              ntiles, err);
+    return cudaGetLastError();
 }
 
 // Weight-gradient partials: every CTA reduces `tiles` pixel tiles of one image
@@ -420,6 +614,7 @@ struct acm_closure {
          *dh1 = nullptr;
     float *net = nullptr, *xbuf = nullptr, *partial = nullptr;
     double *lpart = nullptr;
+    unsigned *derr = nullptr;  // device error word (ERR_TIMEOUT of a bounded wait)
     int loss_blocks = 0, wg_ctas = 0, wg_tiles = 0;
     cudaStream_t stream = nullptr;
     std::string err;
@@ -463,14 +658,17 @@ cudaError_t forward(acm_closure *c, const float *x)
 {
     const int HW = c->nx * c->ny;
     k_pack_nhwc<<<256, 256, 0, c->stream>>>(x, c->x16, HW, c->batch);
-    dim3 grid(c->nx / CTW, c->ny / CTH, c->batch);
-    k_conv<16, 32, OUT_RELU_BF16><<<grid, CTHREADS, 0, c->stream>>>(
-        c->x16, c->A[0], c->bias[0], nullptr, c->h1, c->ny, c->nx, 32);
-    k_conv<32, 32, OUT_RELU_BF16><<<grid, CTHREADS, 0, c->stream>>>(
-        c->h1, c->A[1], c->bias[1], nullptr, c->h2, c->ny, c->nx, 32);
-    k_conv<32, 16, OUT_F32_NCHW><<<grid, CTHREADS, 0, c->stream>>>(
-        c->h2, c->A[2], c->bias[2], nullptr, c->net, c->ny, c->nx, 3);
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = conv_tc<16, 32, OUT_RELU_BF16>(c->x16, c->A[0], c->bias[0], nullptr, c->h1, c->ny,
+                                           c->nx, 32, c->batch, c->derr, c->stream);
+    if (e == cudaSuccess)
+        e = conv_tc<32, 32, OUT_RELU_BF16>(c->h1, c->A[1], c->bias[1], nullptr, c->h2, c->ny,
+                                           c->nx, 32, c->batch, c->derr, c->stream);
+    if (e == cudaSuccess)
+        e = conv_tc<32, 16, OUT_F32_NCHW>(c->h2, c->A[2], c->bias[2], nullptr, c->net, c->ny,
+                                          c->nx, 3, c->batch, c->derr, c->stream);
+    return e;
 }
 
 // loss and gradients (into c->grad) for input x and target (normalised)
@@ -483,12 +681,13 @@ cudaError_t loss_grad(acm_closure *c, const float *x, const float *target, doubl
     k_loss<<<c->loss_blocks, 256, 0, c->stream>>>(x, c->net, target, c->d16, c->lpart, HW,
                                                   c->batch, (float)(2.0 / nel), c->weights[0],
                                                   c->weights[1], c->weights[2]);
-    dim3 grid(c->nx / CTW, c->ny / CTH, c->batch);
     // data gradients with the ReLU masks of h2 and h1
-    k_conv<16, 32, OUT_MASK_BF16><<<grid, CTHREADS, 0, c->stream>>>(
-        c->d16, c->Bm[2], nullptr, c->h2, c->dh2, c->ny, c->nx, 32);
-    k_conv<32, 32, OUT_MASK_BF16><<<grid, CTHREADS, 0, c->stream>>>(
-        c->dh2, c->Bm[1], nullptr, c->h1, c->dh1, c->ny, c->nx, 32);
+    e = conv_tc<16, 32, OUT_MASK_BF16>(c->d16, c->Bm[2], nullptr, c->h2, c->dh2, c->ny, c->nx,
+                                       32, c->batch, c->derr, c->stream);
+    if (e == cudaSuccess)
+        e = conv_tc<32, 32, OUT_MASK_BF16>(c->dh2, c->Bm[1], nullptr, c->h1, c->dh1, c->ny,
+                                           c->nx, 32, c->batch, c->derr, c->stream);
+    if (e != cudaSuccess) return e;
     // weight gradients
     dim3 wg(c->wg_ctas, c->batch);
     const int np = c->wg_ctas * c->batch;
@@ -518,10 +717,22 @@ cudaError_t loss_grad(acm_closure *c, const float *x, const float *target, doubl
     return e;
 }
 
+// device error word: a bounded wait of a convolution gave up
+acm_status check_err(acm_closure *c)
+{
+    unsigned f = 0;
+    cudaError_t e = cudaMemcpyAsync(&f, c->derr, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                                    c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cfail(c, ACM_ECUDA, cudaGetErrorString(e));
+    if (f & ERR_TIMEOUT) return cfail(c, ACM_ETIMEOUT, "a tensor-core wait timed out");
+    return ACM_OK;
+}
+
 void release(acm_closure *c)
 {
     void *ptrs[] = {c->master, c->grad, c->adam_m, c->adam_v, c->x16, c->h1, c->h2, c->d16,
-                    c->dh2, c->dh1, c->net, c->xbuf, c->partial, c->lpart};
+                    c->dh2, c->dh1, c->net, c->xbuf, c->partial, c->lpart, c->derr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (int l = 0; l < NL; ++l) {
@@ -577,6 +788,7 @@ acm_status acm_closure_create(int nx, int ny, int batch, acm_closure **out)
     al((void **)&c->xbuf, NB * 3 * 4);
     al((void **)&c->partial, (size_t)c->wg_ctas * batch * (32 * 9 * 32 + 32) * 4);
     al((void **)&c->lpart, (size_t)c->loss_blocks * 8);
+    al((void **)&c->derr, sizeof(unsigned));
     if (e != cudaSuccess) {
         release(c);
         delete c;
@@ -654,6 +866,7 @@ acm_status acm_closure_loss_grad(acm_closure *c, const float *x_dev, const float
     if (!c || !x_dev || !target_dev) return cfail(c, ACM_EINVAL, "null argument");
     double l = 0.0;
     CKC(c, loss_grad(c, x_dev, target_dev, &l));
+    if (acm_status st = check_err(c); st != ACM_OK) return st;
     if (loss) *loss = l;
     if (grad_host) {
         CKC(c, cudaMemcpyAsync(grad_host, c->grad, c->nparam * 4, cudaMemcpyDeviceToHost,
@@ -711,8 +924,8 @@ acm_status acm_closure_apply(acm_closure *c, acm_handle *h)
                                                      c->scales[0], c->scales[1], c->weights[0]);
     }
     CKC(c, cudaGetLastError());
-    CKC(c, cudaStreamSynchronize(c->stream));  // the handle's next step reads the fields
-    return ACM_OK;
+    // the handle's next step reads the fields: wait (and check the error word)
+    return check_err(c);
 }
 
 acm_status acm_closure_destroy(acm_closure *c)
