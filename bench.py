@@ -29,6 +29,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N3 = 256
+RESET_STEPS = 2000   # the timed repetitions restart from the initial field this often
 U0 = 0.05
 RE = 1600.0
 BYTES_PER_LU_FP32 = 32      # 4 fields read + 4 fields written, 4 B each
@@ -55,6 +56,7 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.lines = []
+        self.ready = threading.Event()
 
     def __enter__(self):
         try:
@@ -71,6 +73,13 @@ class ClockSampler:
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
+            self.ready.set()
+
+    def wait_ready(self, timeout: float = 3.0):
+        """Block until the sampler has produced its first line (nvidia-smi
+        takes a moment to start), so that the timed region is sampled."""
+        if self.proc is not None:
+            self.ready.wait(timeout)
 
     def __exit__(self, *exc):
         if self.proc:
@@ -98,6 +107,14 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def clock_summary(clk, ms_per_step):
+    """The sampler's summary plus time x median SM clock (ms x MHz per step),
+    the figure that compares runs taken at different clocks."""
+    c = clk.summary()
+    c["ms_per_step_x_sm_mhz"] = ms_per_step * c["sm_mhz"] if c["sm_mhz"] else None
+    return c
 
 
 def measured_peaks():
@@ -789,6 +806,9 @@ def main():
                     help="mames: (a) DPSL wall time, (b) 4096^2 TGV throughput, (c) TGV accuracy")
     ap.add_argument("--zchunks", type=int, default=env_int("ACM_ZCHUNKS", 0))
     ap.add_argument("--t3y", type=int, default=env_int("ACM_T3Y", 16))
+    ap.add_argument("--dt", type=float, default=1.0,
+                    help="tgv3d: time step in lattice units (c = 1/dt); the Re = 1600 vortex is "
+                         "at the stability edge at dt = 1 and runs long at dt = 0.5")
     ap.add_argument("--n", type=int, default=N3,
                     help="grid side (profiling runs use a smaller cube; the bench line is 256)")
     args = ap.parse_args()
@@ -829,10 +849,10 @@ def main():
 
     n3 = args.n
     nu = wl.tgv3d_nu(n3, U0, RE)
-    rho, u, v, w = wl.tgv3d(n3, U0)
+    rho, u, v, w = wl.tgv3d(n3, U0, dt=args.dt)
     nodes = n3 ** 3
     mass0 = float(rho.sum())
-    prm = acm.make_params((n3, n3, n3), nu=nu, precision=acm.FP32_DEV)
+    prm = acm.make_params((n3, n3, n3), nu=nu, precision=acm.FP32_DEV, dt=args.dt)
     solver = acm.Solver(prm)
     stream = torch.cuda.Stream()
     solver.set_stream(stream.cuda_stream)
@@ -849,13 +869,32 @@ def main():
             dist.barrier()
 
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    pinned = [torch.from_numpy(x).pin_memory() for x in (rho, u, v, w)]
+    # the timed region (exactly K steps between barriers) is repeated until
+    # about a second has been timed, so that the clock sampler sees it; the
+    # per-step time is the median over the repetitions.  Between repetitions
+    # (untimed) the state is reset to the initial field every RESET_STEPS
+    # steps: the Re = 1600 vortex at dt = 1 sits at the edge of the scheme's
+    # stability (|u|^2 dt / 2 nu = 0.98) and is not run into its turbulent
+    # phase here; the kernel's work does not depend on the flow state
+    reps, since = [], 0
     with ClockSampler(local) as clk:
-        barrier()
-        ev0.record(stream)
-        solver.step(args.steps)
-        ev1.record(stream)
-        barrier()
-    ms = ev0.elapsed_time(ev1)
+        clk.wait_ready()
+        while True:
+            if since + args.steps > RESET_STEPS:
+                solver.sync()
+                solver.set_fields_raw(0, [p.data_ptr() for p in pinned] + [None])
+                since = 0
+            barrier()
+            ev0.record(stream)
+            solver.step(args.steps)
+            ev1.record(stream)
+            barrier()
+            since += args.steps
+            reps.append(ev0.elapsed_time(ev1))
+            if sum(reps) >= 1000.0 or len(reps) >= 5000:
+                break
+    ms = statistics.median(reps)
     solver.sync()  # raises on blow-up
     ms = multirank.max_over_ranks(ms, dist, device="cuda")
     diag = solver.reduce()
@@ -864,7 +903,6 @@ def main():
     # state; every step, advance it and read its status back (acm_sync: the
     # blow-up check, a synchronising device -> host read); then read the FP64
     # diagnostics and the final fields
-    pinned = [torch.from_numpy(x).pin_memory() for x in (rho, u, v, w)]
     outs = [torch.empty(x.shape, dtype=torch.float64).pin_memory() for x in (rho, u, v, w)]
     barrier()
     t0 = time.perf_counter()
@@ -896,7 +934,7 @@ def main():
     # GPU (outside the timed regions)
     accuracy = None
     if not args.no_fp64_check:
-        ref = acm.Solver(acm.make_params((n3, n3, n3), nu=nu, precision=acm.FP64))
+        ref = acm.Solver(acm.make_params((n3, n3, n3), nu=nu, precision=acm.FP64, dt=args.dt))
         ref.set_stream(stream.cuda_stream)
         ref.set_fields(rho, u, v, w)
         ref.step(64)
@@ -936,7 +974,7 @@ def main():
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (2 x 268 MB state vs 129 MB L2), no flush",
                    "zchunks": args.zchunks or "heuristic", "t3y": args.t3y,
-                   "graph_steps": 64},
+                   "graph_steps": 64, "dt": args.dt, "reset_every_steps": RESET_STEPS},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": f"{peak_kind} copy bandwidth",
                      "frac_of_nominal_8tbs": achieved / 8000.0,
@@ -951,7 +989,9 @@ def main():
                      "unit": "GLUPS", "h2d_bytes_per_step": h2d / args.steps,
                      "d2h_bytes_per_step": d2h / args.steps, "seconds": bulk_s},
         "gpu_launches": args.steps,
-        "clocks": clk.summary(),
+        "timed_repetitions": {"count": len(reps), "ms_per_step_min": min(reps) / args.steps,
+                              "ms_per_step_max": max(reps) / args.steps},
+        "clocks": clock_summary(clk, ms / args.steps),
         "diagnostics": {"mass_rel_drift": float(max(abs(diag[0] - mass0), abs(diag_e2e[0] - mass0),
                                                     abs(diag_bulk[0] - mass0)) / mass0),
                         "E_k": float(diag[4]), "max_u": float(diag[6]),

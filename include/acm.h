@@ -340,6 +340,15 @@ acm_status acm_closure_set_scales(acm_closure *c, const float *scales3);
  * leave the density deviation, whose acoustic content differs between grids
  * of different lattice speed, to the scheme) */
 acm_status acm_closure_set_loss_weights(acm_closure *c, const float *w3);
+/* Training-input noise: acm_closure_loss_grad and acm_closure_train_step
+ * add sigma * N(0, 1) (normalised units; counter-based normal variates from
+ * SEED and the call count) to the channels of non-zero loss weight before the
+ * forward pass, and fit x_noisy + net(x_noisy) to the target: the network
+ * learns to pull perturbed states back toward the reference, which keeps
+ * corrected free runs (whose inputs carry the closure's own past errors)
+ * near the states it was trained on.  sigma = 0 (the default) turns it off.
+ * Not part of the paper's method. */
+acm_status acm_closure_set_input_noise(acm_closure *c, float sigma, uint64_t seed);
 /* host FP32 weights in, resets the Adam state; or weights out */
 acm_status acm_closure_set_weights(acm_closure *c, const float *w, size_t n);
 acm_status acm_closure_get_weights(acm_closure *c, float *w, size_t n);

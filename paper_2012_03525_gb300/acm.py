@@ -29,7 +29,7 @@ EXPORTS = ["acm_create", "acm_batch_create", "acm_set_stream", "acm_nruns", "acm
            "acm_closure_last_error", "acm_reduce_mass_noalloc",
            "acm_noalloc_last_error", "acm_storage_elems", "acm_create_ext",
            "acm_current_buffer", "acm_stability_ratio", "acm_reduce_error",
-           "acm_reduce_laplace"]
+           "acm_reduce_laplace", "acm_closure_set_input_noise"]
 
 
 class AcmError(RuntimeError):
@@ -104,6 +104,7 @@ def load():
         "acm_closure_set_stream": ([H, ctypes.c_void_p], ctypes.c_int),
         "acm_closure_set_scales": ([H, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
         "acm_closure_set_loss_weights": ([H, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
+        "acm_closure_set_input_noise": ([H, ctypes.c_float, ctypes.c_uint64], ctypes.c_int),
         "acm_closure_set_weights": ([H, ctypes.POINTER(ctypes.c_float), ctypes.c_size_t],
                                     ctypes.c_int),
         "acm_closure_get_weights": ([H, ctypes.POINTER(ctypes.c_float), ctypes.c_size_t],
@@ -388,6 +389,9 @@ class Closure:
     def set_loss_weights(self, w_rho, w_u):
         arr = (ctypes.c_float * 3)(w_rho, w_u, w_u)
         self._check(self._lib.acm_closure_set_loss_weights(self._c, arr))
+
+    def set_input_noise(self, sigma, seed=0):
+        self._check(self._lib.acm_closure_set_input_noise(self._c, float(sigma), int(seed)))
 
     def set_weights(self, w):
         w = np.ascontiguousarray(w, dtype=np.float32)

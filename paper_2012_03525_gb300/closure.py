@@ -130,10 +130,12 @@ def he_init(seed=0, scale_out=1e-2):
     return np.concatenate(parts).astype(np.float32)
 
 
-def train(setup, X, Y, torch, batch, epochs=20, lr=1e-3, seed=0, closure=None):
+def train(setup, X, Y, torch, batch, epochs=20, lr=1e-3, seed=0, closure=None, noise=0.0):
     """Adam on the stored samples (shuffled each epoch); returns the trained
     closure and the mean loss of every epoch.  A given ``closure`` continues
-    from its current weights."""
+    from its current weights.  ``noise`` > 0 perturbs the training inputs
+    (acm_closure_set_input_noise) so the network also learns to pull
+    perturbed states back toward the reference."""
     nc = setup.n_coarse
     sr, su = setup.scales()
     if closure is None:
@@ -144,6 +146,7 @@ def train(setup, X, Y, torch, batch, epochs=20, lr=1e-3, seed=0, closure=None):
         # lattices, so it is left to the scheme
         closure.set_loss_weights(0.0, 1.0)
         closure.set_weights(he_init(seed))
+    closure.set_input_noise(noise, seed)
     rng = np.random.default_rng(seed)
     losses = []
     for ep in range(epochs):
@@ -152,6 +155,7 @@ def train(setup, X, Y, torch, batch, epochs=20, lr=1e-3, seed=0, closure=None):
         for k in order:
             tot += closure.train_step(X[k].data_ptr(), Y[k].data_ptr(), lr)
         losses.append(tot / len(order))
+    closure.set_input_noise(0.0)
     return closure, losses
 
 
@@ -239,3 +243,72 @@ def evaluate_windows(setup, closure, seeds, windows, torch, batch):
     for h in (fine, plain, corr):
         h.close()
     return {"plain": float(np.mean(ep)), "closure": float(np.mean(ec))}
+
+
+def rollout_curve(setup, closure, seeds, windows, torch, batch):
+    """Free runs from the filtered fine state at t = 0 to t = windows x
+    window x dt: velocity error (relative L2 against the filtered fine FP64
+    run, on the coarse grid) after every window and the wall time of the run
+    (stepping only, synchronised), for the plain scheme at n_coarse (FP32 and
+    FP64) and 2 n_coarse (FP64) and for the corrected n_coarse FP32 run (the
+    closure applied after every window).  The fine run itself is the
+    reference (error 0); its wall time is reported too."""
+    nc, f = setup.n_coarse, setup.factor
+    sr, su = setup.scales()
+    fine = _fine(setup, seeds)
+    refs = []
+    for _ in range(windows):
+        fine.step(setup.window)
+        r = torch.empty((batch, 3, nc, nc), device="cuda", dtype=torch.float32)
+        fine.restrict_to(None, f, out_dev=r.data_ptr(), scales=(sr, su))
+        refs.append(r)
+    fine.sync()
+
+    def err(a, ref):
+        d = (a[:, 1:] - ref[:, 1:]).double()
+        return float(torch.sqrt((d * d).sum() / (ref[:, 1:].double() ** 2).sum()))
+
+    configs = {"plain_coarse_fp32": (nc, acm.FP32_DEV, False),
+               "plain_coarse_fp64": (nc, acm.FP64, False),
+               "plain_2coarse_fp64": (2 * nc, acm.FP64, False),
+               "closure_coarse_fp32": (nc, acm.FP32_DEV, True)}
+    out = {}
+    x = torch.empty((batch, 3, nc, nc), device="cuda", dtype=torch.float32)
+    for name, (n, prec, corrected) in configs.items():
+        start = _fine(setup, seeds)
+        errs, secs = [], 0.0
+        for timed in (False, True):
+            run = acm.Solver([setup.params(n, prec) for _ in seeds])
+            start.restrict_to(run, setup.n_fine // n)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            try:
+                for k in range(windows):
+                    run.step(setup.window)
+                    if corrected:
+                        closure.apply(run)
+                    if not timed:
+                        # the run's velocity on the coarse grid, normalised
+                        # (factor 1: a scaled copy of an FP64 or FP32 run)
+                        run.restrict_to(None, n // nc, out_dev=x.data_ptr(), scales=(sr, su),
+                                        u_scale=nc / n, rho_scale=(nc / n) ** 2)
+                        torch.cuda.synchronize()
+                        errs.append(err(x, refs[k]))
+                run.sync()
+            except acm.AcmError:
+                errs.append(float("inf"))
+            if timed:
+                secs = time.perf_counter() - t0
+            run.close()
+        start.close()
+        out[name] = {"error_per_window": errs, "final_error": errs[-1], "seconds": secs}
+    fine.close()
+    # the fine reference run's own wall time over the same horizon
+    ref = _fine(setup, seeds)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ref.step(windows * setup.window)
+    ref.sync()
+    out["plain_fine_fp64"] = {"final_error": 0.0, "seconds": time.perf_counter() - t0}
+    ref.close()
+    return out

@@ -39,7 +39,6 @@ struct acm_handle {
     void *buf[2][NFIELD] = {};
     int cur = 0;
     int64_t steps = 0;
-    int64_t scanned_steps = 0;  // step count at the last non-finite scan (3D)
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     bool own_fields = true;           // false: acm_create_ext (caller-owned buffers)
@@ -560,19 +559,7 @@ acm_status ensure_graph(acm_handle *h)
 
 acm_status check_flags(acm_handle *h)
 {
-    if (h->dim == 3 && h->steps != h->scanned_steps) {
-        // the 3D step kernel does not test its outputs; scan rho' and u
-        cudaError_t e =
-            h->prec == ACM_FP64
-                ? launch_scan_nonfinite<double>(static_cast<const double *>(h->buf[h->cur][F_R]),
-                                                static_cast<const double *>(h->buf[h->cur][F_U]),
-                                                (long long)h->pool, h->derr, h->stream)
-                : launch_scan_nonfinite<float>(static_cast<const float *>(h->buf[h->cur][F_R]),
-                                               static_cast<const float *>(h->buf[h->cur][F_U]),
-                                               (long long)h->pool, h->derr, h->stream);
-        if (e != cudaSuccess) return cuda_fail(h, e, "non-finite scan");
-        h->scanned_steps = h->steps;
-    }
+    // every step kernel ORs ERR_NONFINITE into the error word itself
     unsigned flags = 0;
     CK(h, cudaMemcpyAsync(&flags, h->derr, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
@@ -933,7 +920,6 @@ acm_status acm_set_fields(acm_handle *h, int run, const double *rho, const doubl
     CK(h, cudaStreamSynchronize(h->stream));
     h->sticky = 0;
     h->steps = 0;
-    h->scanned_steps = 0;
     h->have_fields[run] = 1;
     // stability pre-check of the initial velocity: a warning, not an error
     double ratio = 0.0;
@@ -1136,7 +1122,6 @@ acm_status acm_restrict(acm_handle *fine, acm_handle *coarse, int factor, double
     CK(fine, cudaStreamSynchronize(fine->stream));
     if (coarse) {
         coarse->steps = 0;
-        coarse->scanned_steps = 0;
         coarse->sticky = 0;
         for (int r = 0; r < coarse->nruns; ++r) coarse->have_fields[r] = 1;
         CK(coarse, cudaMemset(coarse->derr, 0, sizeof(unsigned)));

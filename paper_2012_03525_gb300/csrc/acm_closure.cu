@@ -559,6 +559,39 @@ __global__ void k_loss(const float *__restrict__ x, const float *__restrict__ ne
     if (threadIdx.x == 0) lpart[blockIdx.x] = red[0];
 }
 
+// Training-input noise: x_noisy = x + sigma N(0, 1) on the channels whose
+// loss weight is non-zero.  Normal variates from a counter-based generator:
+// SplitMix64 (Steele, Lea and Flood 2014) of (seed, call, element) gives two
+// uniforms, the Box-Muller transform one normal.  The corrected state is the
+// noisy one (loss = |x_noisy + net(x_noisy) - target|^2), so the network
+// learns to pull a perturbed state back toward the reference.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t z)
+{
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__global__ void k_add_noise(const float *__restrict__ x, float *__restrict__ xn, int HW,
+                            int batch, float sigma, uint64_t key, float w0, float w1, float w2)
+{
+    const float wc[3] = {w0, w1, w2};
+    const long long n = (long long)batch * 3 * HW;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)((i / HW) % 3);
+        float v = x[i];
+        if (wc[c] != 0.f) {
+            const uint64_t h = splitmix64(key ^ splitmix64((uint64_t)i));
+            const float u1 = ((float)(h >> 40) + 0.5f) * (1.0f / 16777216.0f);  // (0, 1)
+            const float u2 = (float)((h >> 16) & 0xFFFFFF) * (1.0f / 16777216.0f);
+            v += sigma * sqrtf(-2.f * logf(u1)) * cospif(2.f * u2);
+        }
+        xn[i] = v;
+    }
+}
+
 __global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
                        float *__restrict__ v, int n, float lr, float b1, float b2, float eps,
                        float c1, float c2)
@@ -615,6 +648,9 @@ struct acm_closure {
     float *net = nullptr, *xbuf = nullptr, *partial = nullptr;
     double *lpart = nullptr;
     unsigned *derr = nullptr;  // device error word (ERR_TIMEOUT of a bounded wait)
+    float noise = 0.f;         // training-input noise (standard deviation, normalised units)
+    uint64_t noise_seed = 0, noise_calls = 0;
+    float *xnoisy = nullptr;
     int loss_blocks = 0, wg_ctas = 0, wg_tiles = 0;
     cudaStream_t stream = nullptr;
     std::string err;
@@ -671,9 +707,24 @@ cudaError_t forward(acm_closure *c, const float *x)
     return e;
 }
 
+uint64_t splitmix64_host(uint64_t z)
+{
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
 // loss and gradients (into c->grad) for input x and target (normalised)
 cudaError_t loss_grad(acm_closure *c, const float *x, const float *target, double *loss)
 {
+    const int HW0 = c->nx * c->ny;
+    if (c->noise > 0.f) {
+        const uint64_t key = splitmix64_host(c->noise_seed) ^ (0xD1B54A32D192ED03ull * ++c->noise_calls);
+        k_add_noise<<<256, 256, 0, c->stream>>>(x, c->xnoisy, HW0, c->batch, c->noise, key,
+                                                c->weights[0], c->weights[1], c->weights[2]);
+        x = c->xnoisy;
+    }
     cudaError_t e = forward(c, x);
     if (e != cudaSuccess) return e;
     const int HW = c->nx * c->ny;
@@ -732,7 +783,8 @@ acm_status check_err(acm_closure *c)
 void release(acm_closure *c)
 {
     void *ptrs[] = {c->master, c->grad, c->adam_m, c->adam_v, c->x16, c->h1, c->h2, c->d16,
-                    c->dh2, c->dh1, c->net, c->xbuf, c->partial, c->lpart, c->derr};
+                    c->dh2, c->dh1, c->net, c->xbuf, c->partial, c->lpart, c->derr,
+                    c->xnoisy};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (int l = 0; l < NL; ++l) {
@@ -789,6 +841,7 @@ acm_status acm_closure_create(int nx, int ny, int batch, acm_closure **out)
     al((void **)&c->partial, (size_t)c->wg_ctas * batch * (32 * 9 * 32 + 32) * 4);
     al((void **)&c->lpart, (size_t)c->loss_blocks * 8);
     al((void **)&c->derr, sizeof(unsigned));
+    al((void **)&c->xnoisy, NB * 3 * 4);
     if (e != cudaSuccess) {
         release(c);
         delete c;
@@ -826,6 +879,16 @@ acm_status acm_closure_set_loss_weights(acm_closure *c, const float *w3)
             return cfail(c, ACM_EINVAL, "loss weights must be finite and >= 0");
         c->weights[i] = w3[i];
     }
+    return ACM_OK;
+}
+
+acm_status acm_closure_set_input_noise(acm_closure *c, float sigma, uint64_t seed)
+{
+    if (!c) return cfail(nullptr, ACM_EINVAL, "null closure");
+    if (!(sigma >= 0.f) || !std::isfinite(sigma)) return cfail(c, ACM_EINVAL, "sigma must be >= 0");
+    c->noise = sigma;
+    c->noise_seed = seed;
+    c->noise_calls = 0;
     return ACM_OK;
 }
 

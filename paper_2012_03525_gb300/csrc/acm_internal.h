@@ -143,9 +143,6 @@ template <typename T>
 cudaError_t launch_laplace(const RunDesc *druns, int nruns, int dim, const T *phi, const T *rho,
                            double *partials, int blocks, double *out, cudaStream_t s);
 
-template <typename T>
-cudaError_t launch_scan_nonfinite(const T *a, const T *b, long long n, unsigned *err,
-                                  cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_import(const double *src, T *dst, const RunDesc &run, int dim, double shift,

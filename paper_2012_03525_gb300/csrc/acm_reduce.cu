@@ -241,72 +241,7 @@ __global__ void k_export(const T *__restrict__ src, double *__restrict__ dst, Ru
         dst[i] = (double)src[storage_index(R, dim, i)] + shift;
 }
 
-// 16-byte vectors of the storage type for the scan below
-template <typename T>
-struct Vec16;
-template <>
-struct Vec16<float> {
-    using type = float4;
-    static constexpr int N = 4;
-};
-template <>
-struct Vec16<double> {
-    using type = double2;
-    static constexpr int N = 2;
-};
-__device__ __forceinline__ bool finite16(const float4 &v)
-{
-    return isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && isfinite(v.w);
-}
-__device__ __forceinline__ bool finite16(const double2 &v)
-{
-    return isfinite(v.x) && isfinite(v.y);
-}
-
-// blow-up detection for kernels that do not flag it themselves: any
-// non-finite value in two fields sets ERR_NONFINITE.  HBM-bound: 16-byte
-// loads, four of each field in flight per thread, when both fields start on
-// a 16-byte boundary; element loads for the rest.
-template <typename T>
-__global__ void k_scan_nonfinite(const T *__restrict__ a, const T *__restrict__ b, long long n,
-                                 unsigned *err)
-{
-    using V = typename Vec16<T>::type;
-    constexpr int NV = Vec16<T>::N;
-    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long nthr = (long long)gridDim.x * blockDim.x;
-    bool bad = false;
-    long long head = 0;  // elements covered by the vector loads
-    if (((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b)) & 15) == 0) {
-        const long long nv = n / NV;
-        const V *av = reinterpret_cast<const V *>(a), *bv = reinterpret_cast<const V *>(b);
-        long long i = tid;
-        for (; i + 3 * nthr < nv; i += 4 * nthr) {
-            const V a0 = av[i], a1 = av[i + nthr], a2 = av[i + 2 * nthr], a3 = av[i + 3 * nthr];
-            const V b0 = bv[i], b1 = bv[i + nthr], b2 = bv[i + 2 * nthr], b3 = bv[i + 3 * nthr];
-            bad |= !(finite16(a0) && finite16(a1) && finite16(a2) && finite16(a3) &&
-                     finite16(b0) && finite16(b1) && finite16(b2) && finite16(b3));
-        }
-        for (; i < nv; i += nthr) bad |= !(finite16(av[i]) && finite16(bv[i]));
-        head = nv * NV;
-    }
-    for (long long i = head + tid; i < n; i += nthr) bad |= !isfinite(a[i]) || !isfinite(b[i]);
-    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(err, ERR_NONFINITE);
-}
-
 }  // namespace
-
-template <typename T>
-cudaError_t launch_scan_nonfinite(const T *a, const T *b, long long n, unsigned *err,
-                                  cudaStream_t s)
-{
-    k_scan_nonfinite<T><<<1216, 256, 0, s>>>(a, b, n, err);
-    return cudaGetLastError();
-}
-template cudaError_t launch_scan_nonfinite<float>(const float *, const float *, long long,
-                                                  unsigned *, cudaStream_t);
-template cudaError_t launch_scan_nonfinite<double>(const double *, const double *, long long,
-                                                   unsigned *, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_reduce(const RunDesc *druns, int nruns, int dim, Fields<T> cur, const T *pu,

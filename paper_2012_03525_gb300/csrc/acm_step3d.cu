@@ -20,8 +20,9 @@
 //     d_a rho^{n+1} - d_a rho^n of Eq. (2.11) is a centred difference of
 //     Delta rho.
 //   * Eq. (2.11) for plane z; u^{n+1} = u + (RHS - Delta rho u) / rho^{n+1}.
-//   * The kernel does not test its outputs for blow-up; the library scans
-//     the fields for non-finite values when the caller synchronises.
+//   * Every thread ORs whether its outputs are finite (the sum of a node's
+//     four new values is finite only if each is); one flag per CTA
+//     (ERR_NONFINITE) reports a blow-up without a separate pass.
 // Storage is padded by T3PAD ghost nodes in x and y (not in z).  Every output
 // node on the first/last two columns/rows is also written to its periodic
 // image in the ghost layers, so the next step's TMA boxes never wrap in x/y;
@@ -313,27 +314,34 @@ struct Unroll<N, N> {
 
 // Write a node's periodic images in the ghost layers (both images exist when
 // the grid is narrower than 2 * T3PAD); only the threads on the first/last
-// T3PAD columns/rows call it.
+// T3PAD columns/rows call it.  Explicit cases, no index arrays (which the
+// compiler would place in local memory).
 template <typename T>
 __device__ __forceinline__ void store_images(Fields<T> out, long long gi, int gx, int gy, int nx,
                                           int ny, long long PX, T rn, T un, T vn, T wn)
 {
-    int xs[3], ys[3], nxs = 1, nys = 1;
-    xs[0] = 0;
-    ys[0] = 0;
-    if (gx < T3PAD) xs[nxs++] = nx;
-    if (gx >= nx - T3PAD) xs[nxs++] = -nx;
-    if (gy < T3PAD) ys[nys++] = ny;
-    if (gy >= ny - T3PAD) ys[nys++] = -ny;
-    for (int jy = 0; jy < nys; ++jy)
-        for (int jx = 0; jx < nxs; ++jx) {
-            if (jx == 0 && jy == 0) continue;
-            const long long gk = gi + (long long)ys[jy] * PX + xs[jx];
-            out.f[F_R][gk] = rn;
-            out.f[F_U][gk] = un;
-            out.f[F_V][gk] = vn;
-            out.f[F_W][gk] = wn;
-        }
+    auto put = [&](long long off) {
+        out.f[F_R][gi + off] = rn;
+        out.f[F_U][gi + off] = un;
+        out.f[F_V][gi + off] = vn;
+        out.f[F_W][gi + off] = wn;
+    };
+    const bool xl = gx < T3PAD, xr = gx >= nx - T3PAD;
+    const bool yl = gy < T3PAD, yr = gy >= ny - T3PAD;
+    if (xl) put(nx);
+    if (xr) put(-nx);
+    if (yl) {
+        const long long o = (long long)ny * PX;
+        put(o);
+        if (xl) put(o + nx);
+        if (xr) put(o - nx);
+    }
+    if (yr) {
+        const long long o = -(long long)ny * PX;
+        put(o);
+        if (xl) put(o + nx);
+        if (xr) put(o - nx);
+    }
 }
 
 template <typename T, int TY, bool GEN>
@@ -392,6 +400,7 @@ __global__ void __launch_bounds__(T3X *TY / 2, Prec<T>::MINB * 16 / TY)
         ring_c = (ly + 1) * RW + (lx + 1);
     }
     const long long PX = R.px, PXY = R.px * R.py;
+    bool bad = false;  // a non-finite output of this thread
 
     // Every chunk puts plane zbeg-2 in slot 0, so plane p sits in slot
     // (p - zbeg + 2) % NSLOT; the loop below is unrolled by NSLOT so every
@@ -568,6 +577,10 @@ __global__ void __launch_bounds__(T3X *TY / 2, Prec<T>::MINB * 16 / TY)
                              mk(D[SM][0], D[SM][1])};
             P2 rn, un, vn, wn;
             node_update2<T, GEN>(r, u, v, w, d, K, rn, un, vn, wn);
+            {   // blow-up check on the nodes inside the grid
+                const P2 c2 = add2(add2(rn, un), add2(vn, wn));
+                bad |= !isfinite(add1(own_a ? c2.x : T(0), own_b ? c2.y : T(0)));
+            }
             store2(base_a + (long long)z * PXY, rn.x, un.x, vn.x, wn.x, rn.y, un.y, vn.y, wn.y);
             return true;
         };
@@ -577,6 +590,7 @@ __global__ void __launch_bounds__(T3X *TY / 2, Prec<T>::MINB * 16 / TY)
         __syncthreads();  // every read of this chunk's planes is done
         if (*s_abort) break;
     }
+    if (__syncthreads_or(bad) && tid == 0) atomicOr(err, ERR_NONFINITE);
 }
 
 template <typename T, int TY, bool GEN>
