@@ -380,10 +380,16 @@ def run_batched_drops(args):
 
 def run_closure(args):
     """Learned closure on 2D decaying turbulence (fine 1024^2 FP64 runs of the
-    scheme as reference, coarse 256^2 FP32 runs corrected every 8 steps):
-    trains on the GPU, then compares one-window velocity errors and wall time
-    per window of the corrected coarse run against the plain scheme at 256^2
-    (FP32) and 512^2 (FP64), on held-out initial conditions."""
+    scheme as reference, coarse 256^2 FP32 runs corrected every 8 steps, and
+    a second closure trained for and applied after every single step): trains
+    on the GPU, then compares, on held-out initial conditions,
+      * one-window velocity errors (every window restarted from the filtered
+        fine state) and wall time per window against the plain scheme at
+        256^2 (FP32) and 512^2 (FP64);
+      * free rollouts to fixed physical times (the C5 curve): velocity error
+        after every window and wall time of the whole run for plain 256^2
+        FP32/FP64, plain 512^2 FP64, the corrected 256^2 FP32 run (full and
+        damped correction), and the 1024^2 FP64 reference's own time."""
     import numpy as np
     import torch
     from paper_2012_03525_gb300 import acm, build
@@ -401,11 +407,18 @@ def run_closure(args):
     clo, losses = cl.train(setup, X, Y, torch, B, epochs=20, lr=1e-3)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
+    del X, Y
     ew = cl.evaluate_windows(setup, clo, test_seeds, 6, torch, B)
-    try:
-        roll = cl.evaluate(setup, clo, test_seeds, windows=6, torch=torch, batch=B)
-    except acm.AcmError as e:  # a corrected free run may blow up
-        roll = {"unstable": str(e)}
+    curve = cl.rollout_curve(setup, clo, test_seeds, 12, torch, B)
+    # the same closure with its correction scaled by 1/4 (the output layer is
+    # linear): a damped correction
+    w_full = clo.get_weights()
+    nlast = 3 * 32 * 9 + 3
+    w_damp = w_full.copy()
+    w_damp[-nlast:] *= 0.25
+    clo.set_weights(w_damp)
+    curve_damped = cl.rollout_curve(setup, clo, test_seeds, 12, torch, B)["closure_coarse_fp32"]
+    clo.set_weights(w_full)
 
     # plain FP64 at 512^2 on the same one-window task, compared at 256^2
     nc = setup.n_coarse
@@ -425,7 +438,7 @@ def run_closure(args):
         d = (xm[:, 1:] - ref[:, 1:]).double()
         errs.append(float(torch.sqrt((d * d).sum() / (ref[:, 1:].double() ** 2).sum())))
 
-    def per_window(fn, reps=20):
+    def per_call(fn, reps=20):
         fn()
         torch.cuda.synchronize()
         t = time.perf_counter()
@@ -436,14 +449,39 @@ def run_closure(args):
 
     coarse = acm.Solver([setup.params(nc, acm.FP32_DEV) for _ in test_seeds])
     fine.restrict_to(coarse, 4)
-    t_c = per_window(lambda: (coarse.step(setup.window), coarse.sync()))
+    t_c = per_call(lambda: (coarse.step(setup.window), coarse.sync()))
     # closure cost: restart from the filtered state each time, so repeated
     # corrections cannot drift; the restriction's own time is subtracted
-    t_r = per_window(lambda: fine.restrict_to(coarse, 4))
-    t_ra = per_window(lambda: (fine.restrict_to(coarse, 4), clo.apply(coarse)))
-    t_cc = t_c + max(t_ra - t_r, 0.0)
-    t_m = per_window(lambda: (mid.step(setup.window), mid.sync()))
-    t_f = per_window(lambda: (fine.step(setup.window), fine.sync()))
+    t_r = per_call(lambda: fine.restrict_to(coarse, 4))
+    t_ra = per_call(lambda: (fine.restrict_to(coarse, 4), clo.apply(coarse)))
+    t_apply = max(t_ra - t_r, 0.0)
+    t_cc = t_c + t_apply
+    t_m = per_call(lambda: (mid.step(setup.window), mid.sync()))
+    t_f = per_call(lambda: (fine.step(setup.window), fine.sync()))
+    t_step = per_call(lambda: (coarse.step(1), coarse.sync()))
+    for h in (fine, mid, coarse):
+        h.close()
+    clo.close()
+
+    # a closure trained for and applied after every coarse step
+    s1 = cl.Setup(window=1)
+    X1, Y1 = cl.generate(s1, train_seeds, 12, torch, B, reset=True)
+    clo1, losses1 = cl.train(s1, X1, Y1, torch, B, epochs=20, lr=1e-3)
+    del X1, Y1
+    ew1 = cl.evaluate_windows(s1, clo1, test_seeds, 8, torch, B)
+    try:
+        roll1 = cl.rollout_curve(s1, clo1, test_seeds, 96, torch, B)["closure_coarse_fp32"]
+        roll1 = {"error_every_8_steps": roll1["error_per_window"][7::8],
+                 "seconds": roll1["seconds"]}
+    except acm.AcmError as e:
+        roll1 = {"unstable": str(e)}
+    clo1.close()
+
+    horizon = {k: {"final_error": v["final_error"], "seconds": v["seconds"],
+                   "error_per_window": v.get("error_per_window")} for k, v in curve.items()}
+    horizon["closure_coarse_fp32_damped_0.25"] = {
+        "final_error": curve_damped["final_error"], "seconds": curve_damped["seconds"],
+        "error_per_window": curve_damped["error_per_window"]}
     res = {
         "metric": "time-to-eps (one-window velocity error vs filtered 1024^2 FP64 reference)",
         "value": t_cc, "unit": "s per window (4 runs)", "n_gpus": 1, "higher_is_better": False,
@@ -456,14 +494,18 @@ def run_closure(args):
                   "generate_s": t_gen, "train_s": t_train},
         "one_window_error": {"coarse256_fp32": ew["plain"], "coarse256_fp32_closure": ew["closure"],
                              "plain512_fp64": float(np.mean(errs))},
-        "rollout_6_windows_error": roll,
         "seconds_per_window": {"coarse256_fp32": t_c, "coarse256_fp32_closure": t_cc,
-                               "plain512_fp64": t_m, "plain1024_fp64": t_f},
+                               "closure_apply": t_apply, "plain512_fp64": t_m,
+                               "plain1024_fp64": t_f},
+        "rollout_12_windows": {"physical_time": 12 * setup.window * setup.dt, "runs": horizon},
+        "per_step_closure": {"one_step_error": {"coarse256_fp32": ew1["plain"],
+                                                "coarse256_fp32_closure": ew1["closure"]},
+                             "seconds_per_coarse_step": t_step,
+                             "seconds_per_coarse_step_with_closure": t_step + t_apply,
+                             "rollout_96_steps": roll1,
+                             "loss_last_epoch": losses1[-1]},
     }
     print(json.dumps(res))
-    for h in (fine, mid, coarse):
-        h.close()
-    clo.close()
     return 0
 
 

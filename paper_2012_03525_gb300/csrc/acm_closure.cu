@@ -10,9 +10,9 @@
 //   * data gradient:  dX = (W flipped, channels swapped) applied to dY -- the
 //                     same kernel with a rearranged weight matrix;
 //   * weight gradient: dW[co, (tap, ci)] = sum_p dY[co, p] X[p + off(tap), ci]
-//                     -- a GEMM whose reduction runs over pixels (mma.sync
-//                     m16n8k16 fragments); per-CTA partials are summed in a
-//                     fixed order (deterministic).
+//                     -- a GEMM whose reduction runs over pixels, on tcgen05
+//                     with MN-major operands (k_wgrad_tc); per-CTA partials
+//                     are summed in a fixed order (deterministic).
 // Activations and gradients are stored as BF16 NHWC (channels contiguous),
 // the master weights, Adam moments, losses and corrections in FP32.
 #include <cuda_bf16.h>
@@ -29,35 +29,12 @@ namespace {
 
 typedef __nv_bfloat16 bf16;
 
-constexpr int CTH = 8, CTW = 16, CTP = CTH * CTW;  // pixel tile
-constexpr int CTHREADS = 256;                     // 8 warps, warp w = tile row w
-constexpr int HALO = (CTH + 2) * (CTW + 2);
+constexpr int CTH = 8, CTW = 16;  // pixel tile (128 pixels: the M of the MMAs)
 
 // real / padded channel counts of the three layers
 constexpr int NL = 3;
 constexpr int CIN[NL] = {3, 32, 32}, COUT[NL] = {32, 32, 3};
 constexpr int CINP[NL] = {16, 32, 32}, COUTP[NL] = {32, 32, 16};
-
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4],
-                                         const uint32_t (&b)[2])
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-__device__ __forceinline__ uint32_t ld32(const bf16 *p)
-{
-    return *reinterpret_cast<const uint32_t *>(p);
-}
-
-__device__ __forceinline__ int wrapi(int c, int n)
-{
-    c %= n;
-    return c < 0 ? c + n : c;
-}
 
 enum { OUT_RELU_BF16 = 0, OUT_MASK_BF16 = 1, OUT_F32_NCHW = 2 };
 
@@ -170,6 +147,33 @@ __device__ __forceinline__ void tc_load_row<16>(uint32_t ta, float (&v)[16])
 // bounded wait: ~2^22 polls (well over a second), then give up
 constexpr int TC_WAIT_LIMIT = 1 << 22;
 
+// index in [-1, n] wrapped into [0, n)
+__device__ __forceinline__ int wrap1(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+// Three dx-shifted copies of the (8 + 2) x 16 halo of the 8 x 16 tile at
+// (y0, x0) of image xi (NHWC, periodic): chunk j (channels 8j .. 8j + 7) of
+// halo pixel (hr, c) of copy dx at [dx][j][hr * 16 + c][8].  Each thread owns
+// one (c, j) pair (consecutive threads: consecutive 16-byte chunks in global
+// memory) and every NSUB-th halo row of each copy.
+template <int CI>
+__device__ __forceinline__ void stage_halo(unsigned char *dst, const bf16 *xi, int H, int W,
+                                           int y0, int x0, int tid)
+{
+    constexpr int NJ = CI / 8, NCJ = CTW * NJ, NSUB = TC_THREADS / NCJ;
+    constexpr int XCOPY = TC_HP * CI * 2;
+    const int cj = tid % NCJ, sub = tid / NCJ;
+    const int j = cj % NJ, c = cj / NJ;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const int gx = wrap1(x0 + c + d - 1, W);
+        for (int hr = sub; hr < CTH + 2; hr += NSUB) {
+            const int gy = wrap1(y0 - 1 + hr, H);
+            cp_async16(dst + d * XCOPY + (j * TC_HP + hr * CTW + c) * 16,
+                       xi + ((size_t)gy * W + gx) * CI + 8 * j);
+        }
+    }
+}
+
 template <int CI, int CO, int MODE>
 __global__ void __launch_bounds__(TC_THREADS)
     k_conv_tc(const bf16 *__restrict__ x, const bf16 *__restrict__ A,
@@ -208,16 +212,7 @@ __global__ void __launch_bounds__(TC_THREADS)
     auto stage = [&](int t, int b) {
         const int img = t / tiles_img, r = t - img * tiles_img;
         const int y0 = (r / tiles_x) * CTH, x0 = (r % tiles_x) * CTW;
-        const bf16 *xi = x + (size_t)img * H * W * CI;
-        unsigned char *dst = tsm + b * G::XBUF;
-        for (int i = tid; i < 3 * TC_HP * (CI / 8); i += TC_THREADS) {
-            const int j = i % (CI / 8), q = i / (CI / 8);  // channel chunk fastest: coalesced
-            const int hp = q % TC_HP, dxi = q / TC_HP;
-            const int hr = hp / CTW, c = hp - hr * CTW;
-            const int gy = wrapi(y0 - 1 + hr, H), gx = wrapi(x0 + c + dxi - 1, W);
-            cp_async16(dst + dxi * G::XCOPY + (j * TC_HP + hp) * 16,
-                       xi + ((size_t)gy * W + gx) * CI + 8 * j);
-        }
+        stage_halo<CI>(tsm + b * G::XBUF, x + (size_t)img * H * W * CI, H, W, y0, x0, tid);
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
 
@@ -330,13 +325,14 @@ cudaError_t conv_tc(const bf16 *x, const bf16 *A, const float *bias, const bf16 
         cudaError_t e = cudaFuncSetAttribute(k_conv_tc<CI, CO, MODE>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
         if (e != cudaSuccess) return e;
-        int dev = 0, sms = 0, per = 0;
+        int dev = 0, sms = 0, smem = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_conv_tc<CI, CO, MODE>,
-                                                          TC_THREADS, G::SMEM);
-        if (e != cudaSuccess) return e;
-        grid_cap = std::max(1, sms) * std::max(1, per);
+        cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        // CTAs resident per SM, bounded by shared memory (1 KB per CTA is
+        // reserved); TMEM (32 of 512 columns each) and registers allow more
+        const int per = std::max(1, std::min(8, smem / (G::SMEM + 1024)));
+        grid_cap = std::max(1, sms) * per;
     }
     const int ntiles = batch * (H / CTH) * (W / CTW);
     const int grid = std::min(ntiles, grid_cap);
@@ -345,113 +341,201 @@ cudaError_t conv_tc(const bf16 *x, const bf16 *A, const float *bias, const bf16 
     return cudaGetLastError();
 }
 
-// Weight-gradient partials: every CTA reduces `tiles` pixel tiles of one image
-// into D[co][(tap, ci)] (and the bias gradient) and writes its partial.
-// dy: [B][H][W][CO] bf16, x: [B][H][W][CI] bf16.
+// Weight gradient on tcgen05: dW[co, (tap, ci)] = sum_p dY[p, co] X[p + off(tap), ci]
+// as, per tap, D[co, ci] += A[co, p] B[ci, p] with the reduction (K) over the
+// 16 pixels of each MMA and the accumulator in TMEM across all the tiles a
+// CTA walks (columns tap * CI .. tap * CI + CI - 1).  Both operands are read
+// MN-major (the channel index contiguous in 16-byte core-matrix rows, one row
+// per pixel), i.e. in the re-blocked NHWC layout the forward kernel stages:
+// dY as [co / 8][pixel][8], X as the three dx-shifted halo copies
+// [dx][ci / 8][halo pixel][8], so tap (dy, dx) is copy dx started (dy + 1) * 16
+// pixels in.  M = 128 is the smallest MMA height; rows co >= CO read other
+// shared memory and land in accumulator rows no one reads.  One CTA per SM
+// (9 * CI columns of TMEM), persistent over the tiles of all images; the
+// bias gradient sum_p dY[p, co] is summed by threads from the staged tile.
 template <int CI, int CO>
-__global__ void __launch_bounds__(CTHREADS)
-    k_wgrad(const bf16 *__restrict__ dy, const bf16 *__restrict__ x, float *__restrict__ partial,
-            int H, int W, int tiles_per_cta)
+struct WgGeo {
+    static constexpr int TP = CTH * CTW;                   // 128 pixels per tile
+    static constexpr int YBUF = 16 * TP * 16;              // dY staging, room for 16 row groups
+    static constexpr int XCOPY = TC_HP * CI * 2;           // one dx copy of the X halo tile
+    static constexpr int BUF = YBUF + 3 * XCOPY;           // one staged tile
+    static constexpr int BAR = 2 * BUF;
+    static constexpr int SMEM = BAR + 16;
+    static constexpr int NCOL = 9 * CI;
+    static constexpr int TCOLS = NCOL <= 256 ? 256 : 512;  // TMEM allocation (power of 2)
+    static_assert(CO % 8 == 0 && CO <= 128, "M rows of the MMA");
+    static_assert(CI == 16 || CI == 32, "N of the MMA");
+};
+
+template <int CI, int CO>
+__global__ void __launch_bounds__(TC_THREADS)
+    k_wgrad_tc(const bf16 *__restrict__ dy, const bf16 *__restrict__ x, float *__restrict__ partial,
+               int H, int W, int ntiles, unsigned *err)
 {
-    constexpr int N = 9 * CI, MT = CO / 16, NT = N / 8;
-    constexpr int NTW = (NT + 7) / 8;     // n-tiles per warp (round robin)
-    constexpr int DST = CTP + 8;          // dyT row stride (co rows, pixels contiguous)
-    constexpr int XR = CTW + 8;           // xS row stride (>= CTW + 2)
-    constexpr int XCH = (CTH + 2) * XR + 8;  // xS channel stride
-    __shared__ __align__(16) bf16 dyT[CO * DST];
-    // X tile with its halo rows, transposed to [ci][r][c], in two copies so the
-    // pixel pair (2t, 2t+1) of a B fragment is one aligned 32-bit word for
-    // every dx: copy 0 starts at column x0-1 (used for dx = -1, +1), copy 1 at
-    // column x0 (used for dx = 0)
-    __shared__ __align__(16) bf16 xS[2 * CI * XCH];
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const int g = lane >> 2, t = lane & 3;
+    using G = WgGeo<CI, CO>;
+    extern __shared__ __align__(1024) unsigned char wsm[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(wsm + G::BAR);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(wsm + G::BAR + 8);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tiles_x = W / CTW, tiles_img = tiles_x * (H / CTH);
-    const int img = blockIdx.y;
-    const bf16 *dyi = dy + (size_t)img * H * W * CO;
-    const bf16 *xi = x + (size_t)img * H * W * CI;
 
-    float acc[MT][NTW][4];
-#pragma unroll
-    for (int m = 0; m < MT; ++m)
-#pragma unroll
-        for (int q = 0; q < NTW; ++q)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) acc[m][q][e] = 0.f;
-    float bacc = 0.f;  // thread co < CO: bias-gradient running sum
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         tc_smem(tslot)),
+                     "r"(G::TCOLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    // stage tile t into buffer b: dY re-blocked [co/8][p][8]; X as three
+    // dx-shifted halo copies [dx][ci/8][hp][8] (periodic wrap while staging)
+    // dY chunks: each thread owns one (column c, channel chunk j) pair of
+    // the tile and every YSUB-th row (consecutive threads: consecutive
+    // 16-byte chunks in global memory)
+    constexpr int YNJ = CO / 8, YNCJ = CTW * YNJ, YSUB = TC_THREADS / YNCJ;
+    const int ycj = tid % YNCJ, ysub = tid / YNCJ;
+    const int yj = ycj % YNJ, yc = ycj / YNJ;
+    auto stage = [&](int t, int b) {
+        const int img = t / tiles_img, r = t - img * tiles_img;
+        const int y0 = (r / tiles_x) * CTH, x0 = (r % tiles_x) * CTW;
+        unsigned char *buf = wsm + b * G::BUF;
+        const bf16 *dyi = dy + (size_t)img * H * W * CO;
+        for (int row = ysub; row < CTH; row += YSUB)
+            cp_async16(buf + (yj * G::TP + row * CTW + yc) * 16,
+                       dyi + ((size_t)(y0 + row) * W + x0 + yc) * CO + 8 * yj);
+        stage_halo<CI>(buf + G::YBUF, x + (size_t)img * H * W * CI, H, W, y0, x0, tid);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
 
-    for (int k = 0; k < tiles_per_cta; ++k) {
-        const int tile = blockIdx.x * tiles_per_cta + k;
-        if (tile >= tiles_img) break;
-        const int x0 = (tile % tiles_x) * CTW, y0 = (tile / tiles_x) * CTH;
+    int t = blockIdx.x;
+    if (t < ntiles) stage(t, 0);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+    // kind::f16: D F32, A and B BF16, both MN-major (bits 15, 16), N = CI, M = 128
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
+                           ((uint32_t)(CI >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    uint32_t phase = 0;
+    bool first = true, ok = true;
+    float bacc[8] = {};  // bias-gradient sums of this thread's channels 8 yj .. 8 yj + 7
+    int b = 0;
+    for (; t < ntiles; t += gridDim.x, b ^= 1) {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
-        // dY tile transposed: dyT[co][p], p = 16 r + c
-        for (int i = tid; i < CTP * CO; i += CTHREADS) {
-            const int p = i / CO, co = i - p * CO;
-            const int py = y0 + p / CTW, px = x0 + p % CTW;
-            dyT[co * DST + p] = dyi[((size_t)py * W + px) * CO + co];
-        }
-        for (int i = tid; i < (CTH + 2) * (CTW + 2) * CI; i += CTHREADS) {
-            const int hp = i / CI, ci = i - hp * CI;
-            const int r = hp / (CTW + 2), hc = hp - r * (CTW + 2);  // column x0 - 1 + hc
-            const bf16 val = xi[((size_t)wrapi(y0 - 1 + r, H) * W + wrapi(x0 - 1 + hc, W)) * CI + ci];
-            xS[ci * XCH + r * XR + hc] = val;
-            if (hc >= 1 && hc <= CTW) xS[(CI + ci) * XCH + r * XR + hc - 1] = val;
-        }
-        __syncthreads();
-        if (tid < CO) {
-            float s = 0.f;
-            for (int p = 0; p < CTP; ++p) s += __bfloat162float(dyT[tid * DST + p]);
-            bacc += s;
-        }
-        // K loop: one k16 block = one tile row (16 pixels)
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const unsigned char *buf = wsm + b * G::BUF;
+        if (tid == 0) {
+            const uint32_t yb = tc_smem(buf), xb = tc_smem(buf + G::YBUF);
 #pragma unroll 1
-        for (int row = 0; row < CTH; ++row) {
-            uint32_t a[MT][4];
-#pragma unroll
-            for (int m = 0; m < MT; ++m) {
-                const bf16 *ap = &dyT[(m * 16 + g) * DST + row * CTW + 2 * t];
-                a[m][0] = ld32(ap);
-                a[m][1] = ld32(ap + 8 * DST);
-                a[m][2] = ld32(ap + 8);
-                a[m][3] = ld32(ap + 8 * DST + 8);
-            }
-#pragma unroll
-            for (int q = 0; q < NTW; ++q) {
-                const int nt = w + 8 * q;
-                if (nt < NT) {
-                    const int n = nt * 8 + g;            // column (tap, ci)
-                    const int tap = n / CI, ci = n - tap * CI;
-                    const int dyy = tap / 3 - 1, dx = tap % 3 - 1;
-                    // pixel column 2t + dx of the row: copy 1 at 2t (dx = 0),
-                    // copy 0 at 2t + 1 + dx (dx = -1 or +1, even)
-                    const bf16 *bp = dx == 0
-                        ? &xS[(CI + ci) * XCH + (row + 1 + dyy) * XR + 2 * t]
-                        : &xS[ci * XCH + (row + 1 + dyy) * XR + 2 * t + 1 + dx];
-                    const uint32_t b[2] = {ld32(bp), ld32(bp + 8)};
-#pragma unroll
-                    for (int m = 0; m < MT; ++m) mma_bf16(acc[m][q], a[m], b);
+            for (int tap = 0; tap < 9; ++tap) {
+                const int dy = tap / 3, dxi = tap % 3;
+#pragma unroll 1
+                for (int k = 0; k < G::TP / 16; ++k) {
+                    // MN-major, no swizzle: the leading byte offset is the
+                    // stride between 8-pixel (K) groups (128), the stride
+                    // byte offset that between 8-channel (M/N) groups (as for
+                    // K-major operands; checked against the CPU by a probe)
+                    const uint64_t ad = tc_desc(yb + k * 256, 128, G::TP * 16);
+                    const uint64_t bd =
+                        tc_desc(xb + dxi * G::XCOPY + dy * CTW * 16 + k * 256, 128, TC_HP * 16);
+                    tc_mma(tmem + tap * CI, ad, bd, idesc, (first && k == 0) ? 0u : 1u);
                 }
             }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    tc_smem(bar))
+                : "memory");
+        }
+        first = false;
+        // stage the next tile into the other buffer while the MMAs run
+        const int tn = t + gridDim.x;
+        if (tn < ntiles) stage(tn, b ^ 1);
+        // bias gradient: this thread's own staged dY chunks of the tile
+        for (int row = ysub; row < CTH; row += YSUB) {
+            __align__(16) bf16 h[8];
+            *reinterpret_cast<uint4 *>(h) =
+                *reinterpret_cast<const uint4 *>(buf + (yj * G::TP + row * CTW + yc) * 16);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) bacc[e] += __bfloat162float(h[e]);
+        }
+        bool done = false;
+        for (int it = 0; it < TC_WAIT_LIMIT && !done; ++it) done = tc_try_wait(bar, phase);
+        phase ^= 1;
+        if (__syncthreads_or(!done)) {
+            if (tid == 0) atomicOr(err, ERR_TIMEOUT);
+            ok = false;
+            break;
         }
     }
-    // write the partial: [CO][N] then the bias partial [CO]
-    float *dst = partial + ((size_t)img * gridDim.x + blockIdx.x) * (CO * N + CO);
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // the CTA's partial: [CO][9 CI] then the bias partial [CO]
+    float *dst = partial + (size_t)blockIdx.x * (CO * G::NCOL + CO);
+    if (ok && warp == 0) {  // TMEM lanes 0..31 hold rows co = lane
+#pragma unroll 1
+        for (int c0 = 0; c0 < G::NCOL; c0 += 16) {
+            float v[16];
+            tc_load_row<16>(tmem + c0, v);
+            if (lane < CO)
 #pragma unroll
-    for (int m = 0; m < MT; ++m)
-#pragma unroll
-        for (int q = 0; q < NTW; ++q) {
-            const int nt = w + 8 * q;
-            if (nt < NT)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int co = m * 16 + g + 8 * (e >> 1);
-                    const int n = nt * 8 + 2 * t + (e & 1);
-                    dst[co * N + n] = acc[m][q][e];
-                }
+                for (int e = 0; e < 16; ++e) dst[lane * G::NCOL + c0 + e] = v[e];
         }
-    if (tid < CO) dst[CO * N + tid] = bacc;
+    }
+    // bias partial: sum over the threads that own channel chunk j (after
+    // every read of the staging buffers, which now hold the per-thread sums)
+    __syncthreads();
+    float *bs = reinterpret_cast<float *>(wsm);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) bs[tid * 8 + e] = bacc[e];
+    __syncthreads();
+    if (tid < CO) {
+        const int j = tid / 8, e = tid % 8;
+        float sacc = 0.f;
+        for (int q = j; q < TC_THREADS; q += YNJ) sacc += bs[q * 8 + e];  // threads with yj == j
+        dst[CO * G::NCOL + tid] = sacc;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(G::TCOLS)
+                     : "memory");
+    }
 }
+
+// one CTA per SM for 512-column allocations, two for 256
+template <int CI, int CO>
+cudaError_t wgrad_tc(const bf16 *dy, const bf16 *x, float *partial, int H, int W, int batch,
+                     unsigned *err, int *nparts, cudaStream_t s)
+{
+    using G = WgGeo<CI, CO>;
+    static int grid_cap = 0;
+    if (grid_cap == 0) {
+        cudaError_t e = cudaFuncSetAttribute(k_wgrad_tc<CI, CO>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
+        if (e != cudaSuccess) return e;
+        int dev = 0, sms = 0, smem = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        const int per = std::max(1, std::min(512 / G::TCOLS, smem / (G::SMEM + 1024)));
+        grid_cap = std::max(1, sms) * per;
+    }
+    const int ntiles = batch * (H / CTH) * (W / CTW);
+    const int grid = std::min(ntiles, grid_cap);
+    *nparts = grid;
+    k_wgrad_tc<CI, CO><<<grid, TC_THREADS, G::SMEM, s>>>(dy, x, partial, H, W, ntiles, err);
+    return cudaGetLastError();
+}
+
+// one thread per weight of the largest layer (32 x 32 x 9 + 32)
+constexpr int WGSUM_BLOCKS = (32 * 32 * 9 + 32 + 255) / 256;
 
 // Sum the partials in a fixed order and scatter into the master layout
 // (per layer W[co][ci][3][3] then b[co]; padded channels dropped).
@@ -468,9 +552,15 @@ __global__ void k_wgrad_sum(const float *__restrict__ partial, int nparts, int c
         } else {
             src = coutp * N + (j - cout * cin * 9);
         }
-        float s = 0.f;
-        for (int b = 0; b < nparts; ++b) s += partial[(size_t)b * stride + src];
-        grad[j] = s;
+        // eight interleaved running sums (loads in flight), combined in a
+        // fixed order: the result does not depend on scheduling
+        float s8[8] = {};
+        int b = 0;
+        for (; b + 8 <= nparts; b += 8)
+#pragma unroll
+            for (int q = 0; q < 8; ++q) s8[q] += partial[(size_t)(b + q) * stride + src];
+        for (; b < nparts; ++b) s8[b & 7] += partial[(size_t)b * stride + src];
+        grad[j] = ((s8[0] + s8[1]) + (s8[2] + s8[3])) + ((s8[4] + s8[5]) + (s8[6] + s8[7]));
     }
 }
 
@@ -651,7 +741,7 @@ struct acm_closure {
     float noise = 0.f;         // training-input noise (standard deviation, normalised units)
     uint64_t noise_seed = 0, noise_calls = 0;
     float *xnoisy = nullptr;
-    int loss_blocks = 0, wg_ctas = 0, wg_tiles = 0;
+    int loss_blocks = 0, wg_parts = 0;
     cudaStream_t stream = nullptr;
     std::string err;
 };
@@ -739,23 +829,24 @@ cudaError_t loss_grad(acm_closure *c, const float *x, const float *target, doubl
         e = conv_tc<32, 32, OUT_MASK_BF16>(c->dh2, c->Bm[1], nullptr, c->h1, c->dh1, c->ny,
                                            c->nx, 32, c->batch, c->derr, c->stream);
     if (e != cudaSuccess) return e;
-    // weight gradients
-    dim3 wg(c->wg_ctas, c->batch);
-    const int np = c->wg_ctas * c->batch;
-    size_t off = 0;
-    k_wgrad<32, 16><<<wg, CTHREADS, 0, c->stream>>>(c->d16, c->h2, c->partial, c->ny, c->nx,
-                                                   c->wg_tiles);
-    k_wgrad_sum<<<16, 256, 0, c->stream>>>(c->partial, np, CIN[2], COUT[2], CINP[2], COUTP[2],
+    // weight gradients (tcgen05), per-CTA partials summed in a fixed order
+    int np = 0;
+    e = wgrad_tc<32, 16>(c->d16, c->h2, c->partial, c->ny, c->nx, c->batch, c->derr, &np,
+                         c->stream);
+    if (e != cudaSuccess) return e;
+    k_wgrad_sum<<<WGSUM_BLOCKS, 256, 0, c->stream>>>(c->partial, np, CIN[2], COUT[2], CINP[2], COUTP[2],
                                            c->grad + (COUT[0] * CIN[0] * 9 + COUT[0]) +
                                                (COUT[1] * CIN[1] * 9 + COUT[1]));
-    k_wgrad<32, 32><<<wg, CTHREADS, 0, c->stream>>>(c->dh2, c->h1, c->partial, c->ny, c->nx,
-                                                   c->wg_tiles);
-    k_wgrad_sum<<<16, 256, 0, c->stream>>>(c->partial, np, CIN[1], COUT[1], CINP[1], COUTP[1],
+    e = wgrad_tc<32, 32>(c->dh2, c->h1, c->partial, c->ny, c->nx, c->batch, c->derr, &np,
+                         c->stream);
+    if (e != cudaSuccess) return e;
+    k_wgrad_sum<<<WGSUM_BLOCKS, 256, 0, c->stream>>>(c->partial, np, CIN[1], COUT[1], CINP[1], COUTP[1],
                                            c->grad + (COUT[0] * CIN[0] * 9 + COUT[0]));
-    k_wgrad<16, 32><<<wg, CTHREADS, 0, c->stream>>>(c->dh1, c->x16, c->partial, c->ny, c->nx,
-                                                   c->wg_tiles);
-    k_wgrad_sum<<<16, 256, 0, c->stream>>>(c->partial, np, CIN[0], COUT[0], CINP[0], COUTP[0],
-                                           c->grad + off);
+    e = wgrad_tc<16, 32>(c->dh1, c->x16, c->partial, c->ny, c->nx, c->batch, c->derr, &np,
+                         c->stream);
+    if (e != cudaSuccess) return e;
+    k_wgrad_sum<<<WGSUM_BLOCKS, 256, 0, c->stream>>>(c->partial, np, CIN[0], COUT[0], CINP[0], COUTP[0],
+                                           c->grad);
     e = cudaGetLastError();
     if (e != cudaSuccess || !loss) return e;
     std::vector<double> lp(c->loss_blocks);
@@ -813,8 +904,11 @@ acm_status acm_closure_create(int nx, int ny, int batch, acm_closure **out)
     c->nparam = n_params();
     const size_t HW = (size_t)nx * ny, NB = HW * batch;
     const int tiles_img = (nx / CTW) * (ny / CTH);
-    c->wg_tiles = 4;  // pixel tiles per weight-gradient CTA (enough CTAs to fill the GPU)
-    c->wg_ctas = (tiles_img + c->wg_tiles - 1) / c->wg_tiles;
+    // weight-gradient partials: one per CTA, at most two CTAs per SM
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    c->wg_parts = std::min(tiles_img * batch, 2 * std::max(1, sms));
     c->loss_blocks = 512;
     cudaError_t e = cudaSuccess;
     auto al = [&](void **p, size_t bytes) {
@@ -838,7 +932,7 @@ acm_status acm_closure_create(int nx, int ny, int batch, acm_closure **out)
     al((void **)&c->dh1, NB * 32 * 2);
     al((void **)&c->net, NB * 3 * 4);
     al((void **)&c->xbuf, NB * 3 * 4);
-    al((void **)&c->partial, (size_t)c->wg_ctas * batch * (32 * 9 * 32 + 32) * 4);
+    al((void **)&c->partial, (size_t)c->wg_parts * (32 * 9 * 32 + 32) * 4);
     al((void **)&c->lpart, (size_t)c->loss_blocks * 8);
     al((void **)&c->derr, sizeof(unsigned));
     al((void **)&c->xnoisy, NB * 3 * 4);
