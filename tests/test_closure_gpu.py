@@ -143,3 +143,29 @@ def test_apply_adds_bias_correction_to_solver_state(torch):
             assert np.allclose(got[0] - states[r][0], bias[0] / s_rho, atol=1e-6)
             assert np.allclose(got[1] - states[r][1], bias[1] / s_u, atol=1e-6)
             assert np.allclose(got[2] - states[r][2], bias[2] / s_u, atol=1e-6)
+
+
+def test_input_noise_is_seeded_and_off_by_default(torch):
+    """acm_closure_set_input_noise: sigma = 0 leaves the loss unchanged; a
+    given seed reproduces the same noisy loss (counter-based normals); the
+    noise raises the loss of a closure that fits the clean data."""
+    B, H, W = 2, 16, 32
+    rng = np.random.default_rng(6)
+    x = cr.to_bf16(rng.standard_normal((B, 3, H, W)))
+    target = rng.standard_normal((B, 3, H, W))
+    params = quantised_params(8, 0.5)
+    with acm.Closure(W, H, B) as c:
+        c.set_weights(cr.pack(params).astype(np.float32))
+        xd = torch.from_numpy(x.astype(np.float32)).cuda()
+        td = torch.from_numpy(target.astype(np.float32)).cuda()
+        l0, _ = c.loss_grad(xd.data_ptr(), td.data_ptr())
+        c.set_input_noise(0.0, 3)
+        l1, _ = c.loss_grad(xd.data_ptr(), td.data_ptr())
+        c.set_input_noise(0.5, 3)
+        la, _ = c.loss_grad(xd.data_ptr(), td.data_ptr())
+        c.set_input_noise(0.5, 3)   # resets the call counter
+        lb, _ = c.loss_grad(xd.data_ptr(), td.data_ptr())
+        c.set_input_noise(0.5, 4)
+        lc, _ = c.loss_grad(xd.data_ptr(), td.data_ptr())
+    assert l1 == l0
+    assert la == lb and la != l0 and lc != la
