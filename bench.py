@@ -895,6 +895,13 @@ def main():
     nodes = n3 ** 3
     mass0 = float(rho.sum())
     prm = acm.make_params((n3, n3, n3), nu=nu, precision=acm.FP32_DEV, dt=args.dt)
+    # the same Re on a smaller cube has a smaller nu: warn when dt breaks the
+    # stability condition (a sufficient one; short runs may still finish)
+    ratio = acm.stability_ratio(prm, u, v, w)
+    if ratio > 1.0 and rank == 0:
+        print(f"warning: --n {n3} --dt {args.dt}: stability ratio {ratio:.3f} > 1 "
+              f"(|u|^2 dt / 2 nu, 2 dim nu dt); --dt <= {args.dt / ratio:.3f} is stable",
+              file=sys.stderr)
     solver = acm.Solver(prm)
     stream = torch.cuda.Stream()
     solver.set_stream(stream.cuda_stream)
@@ -1014,13 +1021,16 @@ def main():
         "config": {"workload": WORKLOAD if n3 == N3 else WORKLOAD.replace("256^3", f"{n3}^3"),
                    "nodes": nodes, "grid": [n3, n3, n3],
                    "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "inputs larger than L2 (2 x 268 MB state vs 129 MB L2), no flush",
+                   "l2": (f"inputs larger than L2 (2 x {16 * nodes / 1e6:.0f} MB state vs 129 MB "
+                          "L2), no flush"),
                    "zchunks": args.zchunks or "heuristic", "t3y": args.t3y,
                    "graph_steps": 64, "dt": args.dt, "reset_every_steps": RESET_STEPS},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": f"{peak_kind} copy bandwidth",
                      "frac_of_nominal_8tbs": achieved / 8000.0,
-                     "traffic": profiled_traffic(),
+                     # profiled at 256^3; DRAM traffic grows with the node count
+                     "traffic": (None if profiled_traffic() is None
+                                 else profiled_traffic() * nodes / N3 ** 3),
                      "algorithmic_bytes_per_launch": BYTES_PER_LU_FP32 * nodes},
         "e2e": {"value": multirank.job_throughput(nodes, args.steps, world, e2e_s), "unit": "GLUPS",
                 "h2d_bytes_per_step": h2d / args.steps,

@@ -59,8 +59,18 @@ typedef enum {
 /* boundary condition of one face.  ACM_BC_HALO marks the z faces of a 3D
  * sub-domain: the run is one z-slab of a larger periodic grid, and its two
  * neighbour planes beyond each z face are ghost planes copied from the
- * adjacent slabs (see acm_batch_create) */
-enum { ACM_BC_PERIODIC = 0, ACM_BC_WALL = 1, ACM_BC_LID = 2, ACM_BC_HALO = 3 };
+ * adjacent slabs (see acm_batch_create).  ACM_BC_SYMMETRY is a mirror plane
+ * through the first/last node of the axis (the quarter domains of Sections
+ * 3.6-3.7): the node beyond it is the image of the node one inside, rho,
+ * phi, mu and the tangential velocity are even across it, the normal
+ * velocity is odd and zero on it. */
+enum {
+    ACM_BC_PERIODIC = 0,
+    ACM_BC_WALL = 1,
+    ACM_BC_LID = 2,
+    ACM_BC_HALO = 3,
+    ACM_BC_SYMMETRY = 4
+};
 
 /* storage/arithmetic precision of the fields */
 enum {
@@ -111,10 +121,11 @@ enum { ACM_SCHEME_SMAMES = 0, ACM_SCHEME_MAMES = 1 };
 /* Supported combinations (others return ACM_EINVAL):
  *   dim 2: periodic, wall or lid faces; single- or two-phase (walls of
  *          two-phase runs carry the wetting condition); FP64 or FP32_DEV;
- *   dim 3: periodic x and y faces; single-phase with z periodic or
+ *   dim 3: single-phase: periodic x and y faces, z periodic or
  *          ACM_BC_HALO on both z faces; two-phase (D3Q19 isotropic
  *          operators) with z periodic or walls on both z faces (wetting
- *          condition, stationary); FP64 or FP32_DEV.                 */
+ *          condition, stationary) and x, y faces periodic or symmetry
+ *          planes (both faces of an axis); FP64 or FP32_DEV.          */
 
 /* Create a solver for ONE grid.  Validates the parameters, allocates the
  * double-buffered device fields on the current CUDA device and returns the

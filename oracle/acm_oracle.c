@@ -45,13 +45,15 @@
 #define OR_PERIODIC 0
 #define OR_WALL 1
 #define OR_LID 2
+#define OR_SYMMETRY 4
 
 typedef struct {
     int dim, nx, ny, nz;   /* nodes per direction; nz = 1 in 2D */
     double dt;             /* delta_t in lattice units (delta_x = 1) */
     double nu;             /* kinematic viscosity */
     double rho0;           /* reference density (two-phase: physical density) */
-    int bc[6];             /* faces -x,+x,-y,+y,-z,+z: 0 periodic, 1 wall, 2 lid */
+    int bc[6];             /* faces -x,+x,-y,+y,-z,+z: 0 periodic, 1 wall, 2 lid,
+                              4 symmetry (mirror) plane */
     double lid_u[3];       /* velocity of faces marked as lid */
     double g[3];           /* body force per unit mass */
     int two_phase;         /* 0 or 1 */
@@ -66,13 +68,25 @@ typedef struct {
     const oracle_params *p;
     int n[3];
     int periodic[3];
+    int mirror[3];  /* both faces of the axis are symmetry planes */
 } grid_t;
 
-static inline int wrap(int c, int n, int periodic)
+/* Symmetry (mirror) planes (the quarter domains of Sections 3.6-3.7): the
+   plane passes through the first/last node of the axis, which stay unknowns
+   of the scheme; a node one beyond the plane is the mirror image of the node
+   one inside, c(-1) = c(1), c(n) = c(n-2).  Scalars (rho, phi, mu) and the
+   tangential velocity are even across the plane, the normal velocity (and
+   momentum) component is odd: its image changes sign, and it is zero on the
+   plane. */
+static inline int wrap(int c, int n, int periodic, int mirror)
 {
     if (periodic) {
         if (c < 0) return c + n;
         if (c >= n) return c - n;
+    }
+    if (mirror) {
+        if (c < 0) return -c;
+        if (c >= n) return 2 * (n - 1) - c;
     }
     return c;
 }
@@ -82,48 +96,70 @@ static inline int wrap(int c, int n, int periodic)
    indices inside the grid (interior stencils reach at most the wall) */
 static inline long gidx(const grid_t *G, int i, int j, int k)
 {
-    i = wrap(i, G->n[0], G->periodic[0]);
-    j = wrap(j, G->n[1], G->periodic[1]);
-    k = wrap(k, G->n[2], G->periodic[2]);
+    i = wrap(i, G->n[0], G->periodic[0], G->mirror[0]);
+    j = wrap(j, G->n[1], G->periodic[1], G->mirror[1]);
+    k = wrap(k, G->n[2], G->periodic[2], G->mirror[2]);
     return ((long)k * G->n[1] + j) * G->n[0] + i;
 }
 
-/* a node is a wall node if it lies on a non-periodic face */
+/* a node is a wall node if it lies on a wall or lid face (not on a periodic
+   or a symmetry face) */
 static int on_wall(const grid_t *G, int i, int j, int k)
 {
     int c[3] = {i, j, k};
     for (int d = 0; d < G->p->dim; ++d)
-        if (!G->periodic[d] && (c[d] == 0 || c[d] == G->n[d] - 1)) return 1;
+        if (!G->periodic[d] && !G->mirror[d] && (c[d] == 0 || c[d] == G->n[d] - 1)) return 1;
     return 0;
 }
 
-/* linear index of a node and of its +/- neighbours along each axis */
-typedef struct { long c, p[3], m[3]; } nbr_t;
+/* linear index of a node and of its +/- neighbours along each axis, and
+   whether that neighbour is a mirror image (beyond a symmetry plane) */
+typedef struct { long c, p[3], m[3]; int rp[3], rm[3]; } nbr_t;
 
 static nbr_t neighbours(const grid_t *G, int i, int j, int k)
 {
     nbr_t nb;
+    int cc[3] = {i, j, k};
     nb.c = gidx(G, i, j, k);
     for (int d = 0; d < 3; ++d) {
         int e[3] = {0, 0, 0};
         e[d] = 1;
         nb.p[d] = (d < G->p->dim) ? gidx(G, i + e[0], j + e[1], k + e[2]) : nb.c;
         nb.m[d] = (d < G->p->dim) ? gidx(G, i - e[0], j - e[1], k - e[2]) : nb.c;
+        nb.rp[d] = d < G->p->dim && G->mirror[d] && cc[d] + 1 >= G->n[d];
+        nb.rm[d] = d < G->p->dim && G->mirror[d] && cc[d] - 1 < 0;
     }
     return nb;
 }
 
-/* centred first difference, Eq. (2.12), delta_x = 1 */
+/* value at the + (plus = 1) or - neighbour along d of component field f;
+   odd = the axis whose component f is (-1 for a scalar): across a symmetry
+   plane normal to that axis the image changes sign */
+static double nbv(const double *f, const nbr_t *nb, int d, int plus, int odd)
+{
+    double v = f[plus ? nb->p[d] : nb->m[d]];
+    int refl = plus ? nb->rp[d] : nb->rm[d];
+    return (refl && d == odd) ? -v : v;
+}
+
+/* centred first difference, Eq. (2.12), delta_x = 1, of a scalar field */
 static double dcen(const double *f, const nbr_t *nb, int d)
 {
     return (f[nb->p[d]] - f[nb->m[d]]) / 2.0;
 }
 
-/* 5-point (2D) / 7-point (3D) Laplacian, Eq. (2.13) and its 3D extension */
-static double lap(const grid_t *G, const double *f, const nbr_t *nb)
+/* the same for component `odd` of a vector field */
+static double dcen_c(const double *f, const nbr_t *nb, int d, int odd)
+{
+    return (nbv(f, nb, d, 1, odd) - nbv(f, nb, d, 0, odd)) / 2.0;
+}
+
+/* 5-point (2D) / 7-point (3D) Laplacian, Eq. (2.13) and its 3D extension;
+   odd: as for nbv (-1 for a scalar) */
+static double lap(const grid_t *G, const double *f, const nbr_t *nb, int odd)
 {
     double s = 0.0;
-    for (int d = 0; d < G->p->dim; ++d) s += f[nb->p[d]] + f[nb->m[d]];
+    for (int d = 0; d < G->p->dim; ++d) s += nbv(f, nb, d, 1, odd) + nbv(f, nb, d, 0, odd);
     return s - 2.0 * G->p->dim * f[nb->c];
 }
 
@@ -167,10 +203,17 @@ enum { F_MIRROR = 0, F_WETTING = 1 };
 
 static double field_at(const grid_t *G, const double *f, int kind, int i, int j, int k)
 {
+    /* images across symmetry planes first (scalar fields: even), so that a
+       ghost beyond a wall and a mirror plane takes its image's wall term */
+    for (int d = 0; d < G->p->dim; ++d)
+        if (G->mirror[d]) {
+            int *cd = d == 0 ? &i : (d == 1 ? &j : &k);
+            *cd = wrap(*cd, G->n[d], 0, 1);
+        }
     int c[3] = {i, j, k};
     double add = 0.0;
     for (int d = 0; d < G->p->dim; ++d) {
-        if (G->periodic[d]) continue;
+        if (G->periodic[d] || G->mirror[d]) continue;
         int mirror;
         if (c[d] == -1) mirror = 1;
         else if (c[d] == G->n[d]) mirror = G->n[d] - 2;
@@ -182,7 +225,8 @@ static double field_at(const grid_t *G, const double *f, int kind, int i, int j,
                takes the same edge/corner node */
             int cw[3] = {i, j, k};
             for (int e = 0; e < G->p->dim; ++e)
-                if (!G->periodic[e]) cw[e] = cw[e] < 0 ? 0 : (cw[e] >= G->n[e] ? G->n[e] - 1 : cw[e]);
+                if (!G->periodic[e] && !G->mirror[e])
+                    cw[e] = cw[e] < 0 ? 0 : (cw[e] >= G->n[e] ? G->n[e] - 1 : cw[e]);
             double pw = f[gidx(G, cw[0], cw[1], cw[2])];
             double ct = cos(G->p->theta_deg * 3.14159265358979323846 / 180.0);
             add += 2.0 * (2.0 / G->p->W) * ct * (1.0 - pw * pw);
@@ -259,10 +303,13 @@ static int setup_grid(const oracle_params *p, grid_t *G)
     G->n[1] = p->ny;
     G->n[2] = (p->dim == 3) ? p->nz : 1;
     for (int d = 0; d < 3; ++d) {
+        G->mirror[d] = 0;
         if (d >= p->dim) { G->periodic[d] = 1; continue; }
         int lo = p->bc[2 * d], hi = p->bc[2 * d + 1];
         if ((lo == OR_PERIODIC) != (hi == OR_PERIODIC)) return -1;
+        if ((lo == OR_SYMMETRY) != (hi == OR_SYMMETRY)) return -1;
         G->periodic[d] = (lo == OR_PERIODIC);
+        G->mirror[d] = (lo == OR_SYMMETRY);
         if (G->n[d] < (G->periodic[d] ? 1 : 3)) return -1;
     }
     return 0;
@@ -324,14 +371,14 @@ int oracle_step(const oracle_params *p, double *rho, double *u, double *v,
                     nbr_t nb = neighbours(&G, i, j, k);
                     long c0 = nb.c;
                     double div = 0.0;
-                    for (int d = 0; d < dim; ++d) div += dcen(m[d], &nb, d);
+                    for (int d = 0; d < dim; ++d) div += dcen_c(m[d], &nb, d, d);
                     double r = rho[c0] - dt * div;
-                    if (sat_c) r += 0.5 * cs2 * dt * dt * lap(&G, rho, &nb);
+                    if (sat_c) r += 0.5 * cs2 * dt * dt * lap(&G, rho, &nb, -1);
                     rho1[c0] = r;
                 }
         /* wall density: second-order zero normal gradient, face by face */
         for (int d = 0; d < dim; ++d) {
-            if (G.periodic[d]) continue;
+            if (G.periodic[d] || G.mirror[d]) continue;
             for (int k = 0; k < G.n[2]; ++k)
                 for (int j = 0; j < G.n[1]; ++j)
                     for (int i = 0; i < G.n[0]; ++i) {
@@ -363,10 +410,10 @@ int oracle_step(const oracle_params *p, double *rho, double *u, double *v,
                         /* flux d_beta(rho u_a u_beta + rho cs2 delta_ab) */
                         double flux = 0.0;
                         for (int b = 0; b < dim; ++b)
-                            flux += (m[a][nb.p[b]] * vel[b][nb.p[b]] -
-                                     m[a][nb.m[b]] * vel[b][nb.m[b]]) / 2.0;
+                            flux += (nbv(m[a], &nb, b, 1, a) * nbv(vel[b], &nb, b, 1, b) -
+                                     nbv(m[a], &nb, b, 0, a) * nbv(vel[b], &nb, b, 0, b)) / 2.0;
                         flux += cs2 * dcen(rho, &nb, a);
-                        double mn = m[a][c0] - dt * flux + p->nu * dt * lap(&G, m[a], &nb);
+                        double mn = m[a][c0] - dt * flux + p->nu * dt * lap(&G, m[a], &nb, a);
                         if (sat_m)
                             mn -= (p->nu + 0.5 * cs2 * dt) *
                                   (dcen(rho1, &nb, a) - dcen(rho, &nb, a));
@@ -405,14 +452,18 @@ int oracle_step(const oracle_params *p, double *rho, double *u, double *v,
                     long c0 = gidx(&G, i, j, k);
                     rho[c0] = rho1[c0];
                     if (!on_wall(&G, i, j, k)) {
-                        for (int d = 0; d < dim; ++d) vel[d][c0] = mnew[d][c0] / rho1[c0];
+                        int cc[3] = {i, j, k};
+                        for (int d = 0; d < dim; ++d)
+                            vel[d][c0] = (G.mirror[d] && (cc[d] == 0 || cc[d] == G.n[d] - 1))
+                                             ? 0.0 /* normal velocity on a symmetry plane */
+                                             : mnew[d][c0] / rho1[c0];
                         continue;
                     }
                     /* a node on any stationary wall is at rest; otherwise it
                        is on a lid face and moves with the lid */
                     int cc[3] = {i, j, k}, stationary = 0;
                     for (int d = 0; d < dim; ++d) {
-                        if (G.periodic[d]) continue;
+                        if (G.periodic[d] || G.mirror[d]) continue;
                         if (cc[d] == 0 && p->bc[2 * d] == OR_WALL) stationary = 1;
                         if (cc[d] == G.n[d] - 1 && p->bc[2 * d + 1] == OR_WALL) stationary = 1;
                     }
@@ -515,7 +566,7 @@ int oracle_step_mames(const oracle_params *p, double *rho, double *u, double *v,
                             double grad_div = 0.0;
                             for (int g = 0; g < dim; ++g) grad_div += dmix(&G, m[g], i, j, k, a, g);
                             ms[a][nb.c] = m[a][nb.c] - dt * div_flux(&G, P, &nb, a) +
-                                          nu * dt * lap(&G, m[a], &nb) + 2.0 * nu * dt * grad_div;
+                                          nu * dt * lap(&G, m[a], &nb, a) + 2.0 * nu * dt * grad_div;
                         }
                     }
             /* corrector, Eqs. (2.8) and (2.9) */

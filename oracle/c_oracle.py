@@ -20,7 +20,7 @@ _SO = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-PERIODIC, WALL, LID = 0, 1, 2
+PERIODIC, WALL, LID, SYMMETRY = 0, 1, 2, 4
 
 
 class OracleParams(ctypes.Structure):

@@ -13,7 +13,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libacm.so")
 
 OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5, -6
-BC_PERIODIC, BC_WALL, BC_LID, BC_HALO = 0, 1, 2, 3
+BC_PERIODIC, BC_WALL, BC_LID, BC_HALO, BC_SYMMETRY = 0, 1, 2, 3, 4
 FP64, FP32_DEV = 0, 1
 SCHEME_SMAMES, SCHEME_MAMES = 0, 1
 TUNE_ZCHUNKS, TUNE_T3Y, TUNE_GRAPH_STEPS, TUNE_BLOCKS = 1, 2, 3, 4

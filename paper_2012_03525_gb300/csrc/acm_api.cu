@@ -88,7 +88,8 @@ acm_status cuda_fail(acm_handle *h, cudaError_t e, const char *what)
 
 bool valid_bc(int b)
 {
-    return b == ACM_BC_PERIODIC || b == ACM_BC_WALL || b == ACM_BC_LID || b == ACM_BC_HALO;
+    return b == ACM_BC_PERIODIC || b == ACM_BC_WALL || b == ACM_BC_LID || b == ACM_BC_HALO ||
+           b == ACM_BC_SYMMETRY;
 }
 
 acm_status validate(const acm_params &p, std::string &why)
@@ -117,13 +118,22 @@ acm_status validate(const acm_params &p, std::string &why)
             if (n[d] < 2) return bad("sub-domains need nz >= 2");
             continue;
         }
+        if ((lo == ACM_BC_SYMMETRY) != (hi == ACM_BC_SYMMETRY))
+            return bad("a symmetry face must be paired with a symmetry face");
+        if (lo == ACM_BC_SYMMETRY) {
+            if (p.dim != 3 || !p.two_phase || d == 2)
+                return bad("symmetry planes are for the x and y faces of 3D two-phase runs");
+            if (n[d] < 3) return bad("symmetry planes need >= 3 nodes across");
+            continue;
+        }
         if ((lo == ACM_BC_PERIODIC) != (hi == ACM_BC_PERIODIC))
             return bad("a periodic face must be paired with a periodic face");
         if (lo != ACM_BC_PERIODIC && n[d] < 4) return bad("walls need >= 4 nodes across");
     }
     if (p.dim == 3) {
         for (int f = 0; f < 4; ++f)
-            if (p.bc[f] != ACM_BC_PERIODIC) return bad("3D grids need periodic x and y faces");
+            if (p.bc[f] != ACM_BC_PERIODIC && p.bc[f] != ACM_BC_SYMMETRY)
+                return bad("3D grids need periodic or symmetry x and y faces");
         const int zb = p.bc[4];
         if (zb == ACM_BC_LID) return bad("3D grids have no lid faces");
         if (zb == ACM_BC_WALL && !p.two_phase)

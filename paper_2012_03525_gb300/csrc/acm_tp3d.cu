@@ -2,8 +2,11 @@
 // with the surface-tension force F_ST = -phi grad mu and the Cahn-Hilliard
 // update of Eq. 2.14 by Heun's RK2, u^n frozen), with the D3Q19-weighted
 // isotropic gradient and Laplacian (c_s^2 = 1/3: axis weight 1/18, edge
-// weight 1/36).  x and y are periodic; z is periodic or bounded by
-// stationary walls carrying the wetting condition
+// weight 1/36).  x and y are periodic or symmetry (mirror) planes through
+// the first and last node (the quarter domains of Sections 3.6-3.7: a node
+// beyond the plane is the image of the node one inside, scalars and the
+// tangential velocity even, the normal velocity odd and zero on the plane);
+// z is periodic or bounded by stationary walls carrying the wetting condition
 // d_n phi = -(2/W) cos(theta) (1 - phi_w^2) and d_n mu = 0 (ghost node one
 // beyond the wall = mirror of the node one inside, plus 2 (2/W) cos(theta)
 // (1 - phi_w^2) for phi).
@@ -40,15 +43,25 @@ __host__ __device__ constexpr int vel(int i, int d)
 
 struct Geo3 {
     int nx, ny, nz;
-    bool zwall;
+    bool zwall, mx, my;       // z walls; symmetry planes on the x / y faces
     long long base, px, pxy;  // storage index of (x, y, z) = base + z pxy + y px + x
     __device__ Geo3(const RunDesc &R)
         : nx(R.nx), ny(R.ny), nz(R.nz), zwall(R.bc[4] != ACM_BC_PERIODIC),
+          mx(R.bc[0] == ACM_BC_SYMMETRY), my(R.bc[2] == ACM_BC_SYMMETRY),
           base(R.off + (long long)R.pad * R.px + R.pad), px(R.px), pxy(R.px * R.py)
     {
     }
-    __device__ __forceinline__ int wx(int x) const { return x < 0 ? x + nx : (x >= nx ? x - nx : x); }
-    __device__ __forceinline__ int wy(int y) const { return y < 0 ? y + ny : (y >= ny ? y - ny : y); }
+    // periodic wrap, or the mirror image across a symmetry plane
+    __device__ __forceinline__ int wx(int x) const
+    {
+        if (mx) return x < 0 ? -x : (x >= nx ? 2 * (nx - 1) - x : x);
+        return x < 0 ? x + nx : (x >= nx ? x - nx : x);
+    }
+    __device__ __forceinline__ int wy(int y) const
+    {
+        if (my) return y < 0 ? -y : (y >= ny ? 2 * (ny - 1) - y : y);
+        return y < 0 ? y + ny : (y >= ny ? y - ny : y);
+    }
     __device__ __forceinline__ int wz(int z) const { return z < 0 ? z + nz : (z >= nz ? z - nz : z); }
     // a node in the grid (x, y wrap; z wraps when periodic, else in range)
     __device__ __forceinline__ long long at(int x, int y, int z) const
@@ -73,9 +86,18 @@ constexpr int BX = 32, BY = 8, ZCH = ACM_TP3D_ZCH;
 constexpr int WX = BX + 2, WY = BY + 2, WP = WX * WY;
 
 // index c in [-1, n + BX] wrapped into [0, n) (a full modulo only for grids
-// narrower than a tile)
-__device__ __forceinline__ int wrapc(int c, int n)
+// narrower than a tile), or reflected across the symmetry planes through
+// nodes 0 and n - 1 (positions beyond n belong to no node of the grid and
+// only need a valid index); *refl: c was reflected (odd fields change sign)
+__device__ __forceinline__ int wrapc(int c, int n, bool mirror, bool *refl)
 {
+    if (mirror) {
+        *refl = c < 0 || c >= n;
+        if (c < 0) c = -c;
+        else if (c >= n) c = 2 * (n - 1) - c;
+        return c < 0 ? 0 : (c >= n ? n - 1 : c);
+    }
+    *refl = false;
     if (c < 0) c += n;
     else if (c >= n) c -= n;
     if ((unsigned)c >= (unsigned)n) {
@@ -85,17 +107,26 @@ __device__ __forceinline__ int wrapc(int c, int n)
     return c;
 }
 
-// storage offsets of a node and its six axis neighbours (x, y wrap; z wraps
-// when periodic; at a wall node the z neighbours beyond it are not used)
+// storage offsets of a node and its six axis neighbours (x, y wrap or
+// mirror; z wraps when periodic; at a wall node the z neighbours beyond it
+// are not used); sx / sy: sign of u at the x neighbours / of v at the y
+// neighbours (-1 for an image across a symmetry plane)
 struct Axis7 {
     long long c, xe, xw, yn, ys, zu, zd;
+    float sxe, sxw, syn, sys;
     __device__ __forceinline__ Axis7(const Geo3 &g, int x, int y, int z)
     {
         c = g.base + (long long)z * g.pxy + (long long)y * g.px + x;
-        xe = c + (x == g.nx - 1 ? 1 - g.nx : 1);
-        xw = c - (x == 0 ? 1 - g.nx : 1);
-        yn = c + (y == g.ny - 1 ? (1 - g.ny) * g.px : g.px);
-        ys = c - (y == 0 ? (1 - g.ny) * g.px : g.px);
+        const bool re = g.mx && x == g.nx - 1, rw = g.mx && x == 0;
+        const bool rn = g.my && y == g.ny - 1, rs = g.my && y == 0;
+        xe = c + (x == g.nx - 1 ? (g.mx ? -1 : 1 - g.nx) : 1);
+        xw = c - (x == 0 ? (g.mx ? -1 : 1 - g.nx) : 1);
+        yn = c + (y == g.ny - 1 ? (g.my ? -g.px : (1 - g.ny) * g.px) : g.px);
+        ys = c - (y == 0 ? (g.my ? -g.px : (1 - g.ny) * g.px) : g.px);
+        sxe = re ? -1.f : 1.f;
+        sxw = rw ? -1.f : 1.f;
+        syn = rn ? -1.f : 1.f;
+        sys = rs ? -1.f : 1.f;
         const bool zp = !g.zwall;
         zu = c + (zp && z == g.nz - 1 ? (1 - g.nz) * g.pxy : g.pxy);
         zd = c - (zp && z == 0 ? (1 - g.nz) * g.pxy : g.pxy);
@@ -107,15 +138,20 @@ struct Axis7 {
 // same for every field and plane, so it is formed once per CTA.
 struct WinXY {
     long long xy[2];
-    bool has2;
+    bool rx[2], ry[2];  // the element is an image across an x / y symmetry plane
+    bool has2, anyr;    // second element; some element of this thread is an image
     __device__ __forceinline__ WinXY(const Geo3 &g, int x0, int y0)
     {
         const int tid = threadIdx.y * BX + threadIdx.x;
+        anyr = false;
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
             const int i = min(tid + k * BX * BY, WP - 1);
             const int wy = i / WX, wx = i - wy * WX;
-            xy[k] = g.base + (long long)wrapc(y0 - 1 + wy, g.ny) * g.px + wrapc(x0 - 1 + wx, g.nx);
+            const int yy = wrapc(y0 - 1 + wy, g.ny, g.my, &ry[k]);
+            const int xx = wrapc(x0 - 1 + wx, g.nx, g.mx, &rx[k]);
+            xy[k] = g.base + (long long)yy * g.px + xx;
+            anyr |= rx[k] || ry[k];
         }
         has2 = tid + BX * BY < WP;
     }
@@ -124,8 +160,9 @@ static_assert(WP <= 2 * BX * BY, "a window must fit two loads per thread");
 
 // window of plane z (z in [-1, nz]) of field f: beyond a wall face the
 // mirror plane, plus (KIND == K_WET) the wetting term wet (1 - f_w^2) of the
-// wall plane
-template <typename T, int KIND>
+// wall plane; ODD = 1 (u) / 2 (v): the field changes sign on images across
+// x / y symmetry planes (those elements are loaded synchronously)
+template <typename T, int KIND, int ODD = 0>
 __device__ __forceinline__ void load_window(T *dst, const T *__restrict__ f, const Geo3 &g,
                                             const WinXY &o, int z, T wet)
 {
@@ -137,7 +174,8 @@ __device__ __forceinline__ void load_window(T *dst, const T *__restrict__ f, con
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         if (k == 1 && !o.has2) break;
-        if (!ghost) {  // a plain copy: asynchronous, completed by the z-march's wait
+        const bool flip = (ODD == 1 && o.rx[k]) || (ODD == 2 && o.ry[k]);
+        if (!ghost && !flip) {  // a plain copy: asynchronous, completed by the z-march's wait
             const unsigned d =
                 static_cast<unsigned>(__cvta_generic_to_shared(dst + tid + k * BX * BY));
             asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d),
@@ -146,11 +184,11 @@ __device__ __forceinline__ void load_window(T *dst, const T *__restrict__ f, con
             continue;
         }
         T val = f[o.xy[k] + zo];
-        if (KIND == K_WET) {
+        if (KIND == K_WET && ghost) {
             const T fw = f[o.xy[k] + zwo];
             val += wet * (T(1) - fw * fw);
         }
-        dst[tid + k * BX * BY] = val;
+        dst[tid + k * BX * BY] = flip ? -val : val;
     }
 }
 
@@ -244,8 +282,10 @@ __device__ __forceinline__ T drho_at(const Fields<T> &in, const Geo3 &g, int x, 
 {
     const T *r = in.f[F_R], *u = in.f[F_U], *v = in.f[F_V], *w = in.f[F_W];
     const Axis7 a(g, x, y, z);
-    const T div = T(0.5) * ((rho0 + r[a.xe]) * u[a.xe] - (rho0 + r[a.xw]) * u[a.xw]) +
-                  T(0.5) * ((rho0 + r[a.yn]) * v[a.yn] - (rho0 + r[a.ys]) * v[a.ys]) +
+    const T div = T(0.5) * ((rho0 + r[a.xe]) * (T(a.sxe) * u[a.xe]) -
+                            (rho0 + r[a.xw]) * (T(a.sxw) * u[a.xw])) +
+                  T(0.5) * ((rho0 + r[a.yn]) * (T(a.syn) * v[a.yn]) -
+                            (rho0 + r[a.ys]) * (T(a.sys) * v[a.ys])) +
                   T(0.5) * ((rho0 + r[a.zu]) * w[a.zu] - (rho0 + r[a.zd]) * w[a.zd]);
     const T lap = (r[a.xe] + r[a.xw]) + (r[a.yn] + r[a.ys]) + (r[a.zu] + r[a.zd]) - T(6) * r[a.c];
     return -dt * div + satc * lap;
@@ -310,6 +350,8 @@ __global__ void __launch_bounds__(BX *BY)
 #pragma unroll
                for (int f = 0; f < NWIN; ++f) {
                    if (f == W_PH) load_window<T, K_WET>(win(f, sl), src[f], g, o, z, wet);
+                   else if (f == W_U) load_window<T, K_MIRROR, 1>(win(f, sl), src[f], g, o, z, T(0));
+                   else if (f == W_V) load_window<T, K_MIRROR, 2>(win(f, sl), src[f], g, o, z, T(0));
                    else load_window<T, K_MIRROR>(win(f, sl), src[f], g, o, z, T(0));
                }
            },
@@ -366,6 +408,9 @@ __global__ void __launch_bounds__(BX *BY)
             un = u0 + (rx - d0 * u0) * inv;
             vn = v0 + (ry - d0 * v0) * inv;
             wn = w0 + (rz - d0 * w0) * inv;
+            // the normal velocity is zero on a symmetry plane
+            if (g.mx && (x == 0 || x == g.nx - 1)) un = T(0);
+            if (g.my && (y == 0 || y == g.ny - 1)) vn = T(0);
         }
         // first Heun stage of Eq. (2.14), u^n frozen
         T lph, gpx, gpy, gpz;

@@ -53,7 +53,11 @@ def test_params_struct_layout_matches_header():
     (dict(shape=(8, 8), nu=-1.0), "nu"),
     (dict(shape=(8, 8), bc=[1, 0, 0, 0, 0, 0]), "periodic"),
     (dict(shape=(3, 8), bc=[0, 0, 1, 1, 0, 0]), "walls"),
-    (dict(shape=(4, 8, 8), bc=[1, 1, 0, 0, 0, 0]), "periodic x and y"),
+    (dict(shape=(4, 8, 8), bc=[1, 1, 0, 0, 0, 0]), "periodic or symmetry x and y"),
+    (dict(shape=(4, 8, 8), bc=[4, 4, 0, 0, 0, 0]), "two-phase"),
+    (dict(shape=(4, 8, 8), bc=[4, 0, 0, 0, 0, 0], two_phase=True), "paired"),
+    (dict(shape=(4, 8, 8), bc=[0, 0, 0, 0, 4, 4], two_phase=True), "x and y faces"),
+    (dict(shape=(8, 8), bc=[4, 4, 0, 0, 0, 0], two_phase=True), "3D"),
     (dict(shape=(4, 8, 8), bc=[0, 0, 0, 0, 1, 1]), "two-phase runs only"),
     (dict(shape=(4, 8, 8), bc=[0, 0, 0, 0, 2, 2], two_phase=True), "lid"),
     (dict(shape=(4, 8, 8), bc=[0, 0, 0, 0, 3, 3], two_phase=True), "single-phase only"),

@@ -935,3 +935,82 @@ def test_boussinesq_drop_force_factor(oracle_lib, phi0, r, expect):
     assert np.all(u == 0.0)
     assert np.abs(v + n * g * expect).max() <= 1e-15 * n * g
     assert np.all(rho == 1.0)
+
+
+# ---------------------------------------------------------------- symmetry planes
+def _mirror_extend(f, axes_odd, dims):
+    """Extend a field given on the quarter (mirror planes through the first
+    and last node of each axis in ``dims``) to the periodic box of period
+    2 (n - 1) along those axes; odd along the axes in ``axes_odd``."""
+    out = f
+    for ax in dims:
+        n = out.shape[ax]
+        inner = np.flip(np.take(out, range(1, n - 1), axis=ax), axis=ax)
+        if ax in axes_odd:
+            inner = -inner
+        out = np.concatenate([out, inner], axis=ax)
+    return np.ascontiguousarray(out)
+
+
+@pytest.mark.parametrize("case", ["2d", "2d_two_phase", "3d_two_phase_walls"])
+def test_symmetry_planes_equal_doubled_periodic_box(oracle_lib, case):
+    """Symmetry planes (Sections 3.6-3.7 simulate quarter domains): a run on
+    n nodes with mirror planes through the first and last node of x and y
+    equals, on those nodes, the run on the periodic box of period 2 (n - 1)
+    started from the mirror-symmetric extension of the same fields (scalars
+    even, the normal velocity odd).  Catches a wrong image index, a missing
+    or extra sign of the normal component (in the flux, the Laplacian or the
+    divergence), a wetting term or wall rule applied on a mirror face."""
+    co = oracle_lib
+    rng = np.random.default_rng(17)
+    if case.startswith("2d"):
+        shape = (13, 17)
+        dims = (0, 1)          # array axes y, x
+    else:
+        shape = (9, 11, 12)
+        dims = (1, 2)
+    st = [1 + 0.01 * _smooth(rng, shape)] + [0.03 * _smooth(rng, shape) for _ in range(len(shape))]
+    vel_axes = [len(shape) - 1 - a for a in range(len(shape))]  # u along x = last array axis
+    for a in range(len(shape)):
+        ax = vel_axes[a]
+        if ax in dims:          # normal velocity is zero on its mirror planes
+            idx = [slice(None)] * len(shape)
+            idx[ax] = [0, -1]
+            st[1 + a][tuple(idx)] = 0.0
+    kw = dict(nu=0.04)
+    phi = None
+    if "two_phase" in case:
+        kw.update(two_phase=True, sigma=1e-2, W=4.0, M=0.2)
+        if case.startswith("3d"):
+            kw.update(dt=0.5, theta_deg=120.0, g=(0.0, 0.0, -1e-5))
+            Z, Y, X = np.meshgrid(*[np.arange(k, dtype=float) for k in shape], indexing="ij")
+            phi = -np.tanh(2.0 * (np.sqrt(X ** 2 + Y ** 2 + Z ** 2) - 5.0) / 4.0)
+            for a in range(3):  # walls on z: at rest there
+                st[1 + a][0] = 0.0
+                st[1 + a][-1] = 0.0
+        else:
+            Y, X = np.meshgrid(*[np.arange(k, dtype=float) for k in shape], indexing="ij")
+            phi = -np.tanh(2.0 * (np.hypot(X - 1.0, Y) - 6.0) / 4.0)
+    full_shape = tuple(2 * (shape[a] - 1) if a in dims else shape[a] for a in range(len(shape)))
+    full = [_mirror_extend(st[0], (), dims)]
+    for a in range(len(shape)):
+        full.append(_mirror_extend(st[1 + a], (vel_axes[a],), dims))
+    fphi = None if phi is None else _mirror_extend(phi, (), dims)
+    bc_q = [4, 4, 4, 4, 0, 0] if case.startswith("2d") else [4, 4, 4, 4, 1, 1]
+    bc_f = [0, 0, 0, 0, 0, 0] if case.startswith("2d") else [0, 0, 0, 0, 1, 1]
+    q = [x.copy() for x in st]
+    qphi = None if phi is None else phi.copy()
+    steps = 40
+    co.step(co.make_params(shape, bc=bc_q, **kw), q[0], q[1], q[2],
+            q[3] if len(shape) == 3 else None, qphi, nsteps=steps)
+    co.step(co.make_params(full_shape, bc=bc_f, **kw), full[0], full[1], full[2],
+            full[3] if len(shape) == 3 else None, fphi, nsteps=steps)
+    sl = tuple(slice(0, shape[a]) for a in range(len(shape)))
+    assert np.abs(q[0] - full[0][sl]).max() < 1e-14
+    for a in range(len(shape)):
+        assert np.abs(q[1 + a] - full[1 + a][sl]).max() < 1e-15, a
+    if phi is not None:
+        assert np.abs(qphi - fphi[sl]).max() < 1e-13
+    # the flow moved and the normal velocity stayed zero on its planes
+    assert np.abs(q[1] - st[1]).max() > 1e-6
+    assert np.all(q[1][..., 0] == 0.0) and np.all(q[1][..., -1] == 0.0)

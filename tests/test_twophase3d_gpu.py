@@ -197,3 +197,76 @@ def test_drop_spreading_dewetting_section_3_6(theta):
         assert heights[0] > 1.0
     assert heights[-1] == pytest.approx(want, rel=0.06)
     assert abs(heights[-1] - heights[-2]) < 0.02
+
+
+def _quarter_state(shape, walls=True, amp=2e-3):
+    """A drop centred on the corner of the x and y symmetry planes (on the
+    z = 0 wall), a smooth flow whose normal velocity vanishes on the planes
+    (and on the walls)."""
+    nz, ny, nx = shape
+    Z, Y, X = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    phi = -np.tanh(2.0 * (np.sqrt(X ** 2 + Y ** 2 + (Z - 2.0) ** 2) - 7.0) / 4.0)
+    u = amp * np.sin(np.pi * X / (nx - 1)) * np.cos(np.pi * Y / (ny - 1))
+    v = amp * np.cos(np.pi * X / (nx - 1)) * np.sin(np.pi * Y / (ny - 1)) * np.cos(Z)
+    w = amp * np.cos(np.pi * X / (nx - 1)) * np.cos(2 * np.pi * Y / (ny - 1))
+    if walls:
+        for a in (u, v, w):
+            a[0] = 0.0
+            a[-1] = 0.0
+    return [np.ones(shape), u, v, w, phi]
+
+
+@pytest.mark.parametrize("theta", [90.0, 150.0])
+def test_two_phase_3d_symmetry_planes_fp64(oracle_lib, theta):
+    """Symmetry planes on all four x and y faces (the quarter domains of
+    Sections 3.6-3.7), wetting z walls, gravity along z: parity with the
+    oracle at 1e-12."""
+    shape, bc = (16, 18, 20), [4, 4, 4, 4, 1, 1]
+    st = _quarter_state(shape)
+    ref, got = run_both(oracle_lib, shape, st, 60, nu=0.1, bc=bc, two_phase=True, sigma=1e-2,
+                        W=4.0, M=0.3, theta_deg=theta, g=(0.0, 0.0, -1e-5), dt=0.5)
+    assert_parity(ref, got)
+    # the normal velocity stays zero on its planes
+    assert np.all(got[1][:, :, 0] == 0) and np.all(got[1][:, :, -1] == 0)
+    assert np.all(got[2][:, 0, :] == 0) and np.all(got[2][:, -1, :] == 0)
+
+
+def test_two_phase_3d_symmetry_planes_fp32(oracle_lib):
+    shape, bc = (16, 18, 20), [4, 4, 4, 4, 1, 1]
+    st = _quarter_state(shape)
+    ref, got = run_both(oracle_lib, shape, st, 100, gpu_kw={"precision": acm.FP32_DEV}, nu=0.1,
+                        bc=bc, two_phase=True, sigma=1e-2, W=4.0, M=0.3, theta_deg=120.0,
+                        dt=0.5)
+    assert rel_l2(got[4], ref[4]) < 1e-6
+    for k in (1, 2, 3):
+        assert rel_l2(got[k], ref[k]) < 1e-4
+
+
+def test_symmetry_planes_equal_doubled_box_on_gpu():
+    """On the GPU too, the quarter domain with symmetry planes equals the
+    periodic box of twice the size holding the mirror-symmetric fields."""
+    shape = (12, 14, 16)
+    nz, ny, nx = shape
+    st = _quarter_state(shape, walls=True)
+
+    def ext(f, odd_axes):
+        out = f
+        for ax in (1, 2):
+            n = out.shape[ax]
+            inner = np.flip(np.take(out, range(1, n - 1), axis=ax), axis=ax)
+            out = np.concatenate([out, -inner if ax in odd_axes else inner], axis=ax)
+        return np.ascontiguousarray(out)
+
+    full = [ext(st[0], ()), ext(st[1], (2,)), ext(st[2], (1,)), ext(st[3], ()), ext(st[4], ())]
+    kw = dict(nu=0.1, two_phase=True, sigma=1e-2, W=4.0, M=0.3, theta_deg=120.0,
+              g=(0.0, 0.0, -1e-5), dt=0.5)
+    with acm.Solver(acm.make_params(shape, bc=[4, 4, 4, 4, 1, 1], **kw)) as s:
+        s.set_fields(*st)
+        s.step(40)
+        q = s.fields()
+    with acm.Solver(acm.make_params(full[0].shape, bc=[0, 0, 0, 0, 1, 1], **kw)) as s:
+        s.set_fields(*full)
+        s.step(40)
+        f = s.fields()
+    for k in range(5):
+        assert np.abs(q[k] - f[k][:, :ny, :nx]).max() < 1e-13, k
