@@ -147,6 +147,41 @@ def profiled_traffic():
         return None
 
 
+def accuracy_curve(acm, np, init, n3, nu, args, stream):
+    """FP32 deviation storage against FP64 along one run of K steps: both
+    solvers start from the initial field and are compared every M steps
+    (relative L2 of u and rho - 1; kinetic energy of each from the FP64
+    reductions).  A blow-up ends the curve there."""
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    s32 = acm.Solver(acm.make_params((n3,) * 3, nu=nu, precision=acm.FP32_DEV, dt=args.dt))
+    s64 = acm.Solver(acm.make_params((n3,) * 3, nu=nu, precision=acm.FP64, dt=args.dt))
+    curve = []
+    try:
+        for s in (s32, s64):
+            s.set_stream(stream)
+            s.set_fields(*init)
+        done = 0
+        while done < args.steps:
+            m = min(args.accuracy_every, args.steps - done)
+            try:
+                for s in (s32, s64):
+                    s.step(m)
+                    s.sync()
+            except acm.AcmError as e:
+                curve.append({"step": done + m, "blow_up": str(e)})
+                break
+            done += m
+            f32, f64 = s32.fields()[:4], s64.fields()[:4]
+            curve.append({"step": done, "t": done * args.dt,
+                          "u_rel_l2": max(rel(f32[k], f64[k]) for k in (1, 2, 3)),
+                          "rho_dev_rel_l2": rel(f32[0] - 1.0, f64[0] - 1.0),
+                          "E_k_fp32": float(s32.reduce()[4]), "E_k_fp64": float(s64.reduce()[4])})
+    finally:
+        s32.close()
+        s64.close()
+    return curve
+
+
 def host_threads() -> int:
     """Host cores this process may run on."""
     try:
@@ -838,6 +873,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-check", action="store_true",
                     help="skip the FP64 accuracy run of the tgv3d bench (profiling runs)")
+    ap.add_argument("--accuracy-every", type=int, default=0,
+                    help="tgv3d: also run FP32 and FP64 side by side from the initial field "
+                         "and compare them every this many steps (the FP32-vs-FP64 curve)")
     ap.add_argument("--workload", default="tgv3d", choices=["tgv3d", "drops", "closure", "dpsl", "subdomains", "mames",
                              "twophase3d", "cavity"],
                     help="tgv3d: the bench line; drops: the batched two-phase workload; "
@@ -1005,6 +1043,9 @@ def main():
                     "rho_dev_rel_l2_vs_fp64": rel(f32[0] - 1.0, f64[0] - 1.0),
                     "fp64_GLUPS": nodes * args.steps / (ms64 / 1e3) / 1e9,
                     "fp32_speedup_over_fp64": ms64 / ms}
+        if args.accuracy_every > 0:
+            accuracy["curve"] = accuracy_curve(acm, np, (rho, u, v, w), n3, nu, args,
+                                               stream.cuda_stream)
 
     glups = multirank.job_throughput(nodes, args.steps, world, ms / 1e3)
     per_launch_s = ms / 1e3 / args.steps
