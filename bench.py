@@ -700,33 +700,37 @@ def run_mames(args):
 
 
 def run_twophase3d(args):
-    """3D two-phase throughput on the grid of the paper's coalescence-induced
-    drop-jumping case (Section 3.7: 120 x 120 x 200, nonwetting wall,
-    theta = 180 degrees; two drops touching above the wall), FP32 and FP64,
-    lattice speed c = 2.  The paper's 40 steps took 26 s on 4 CPU nodes
-    (context only)."""
+    """The coalescence-induced drop-jumping case of Section 3.7 on the
+    paper's quarter domain (120 x 120 x 200, symmetry planes on the x and y
+    faces, walls on the z faces, theta = 180 degrees, N_L = 40, c = 10,
+    Cn = 0.1, Pe = 8e3, Oh = 0.037).  Throughput of the 3D two-phase step in
+    FP32 and FP64 (K timed steps after W warm-up steps); with --tci T > 0
+    also the physical run to t = T T_ci for Oh = 0.037 and 0.119 (FP32
+    deviation storage, FP64 for Oh = 0.037 when --tci-fp64 is given): drop
+    centroid velocity W_drop / U_ci, centroid height and the height of the
+    drop's lowest point every T_ci / 8.  The paper's 40 steps took 26 s on 4
+    CPU nodes (context only)."""
     import numpy as np
     import torch
     from paper_2012_03525_gb300 import acm, build
+    from paper_2012_03525_gb300 import workloads as wl
     build.build()
-    nx, ny, nz = 120, 120, 200
-    R = 20.0
-    Z, Y, X = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
-    d1 = np.sqrt((X - (nx / 2 - R)) ** 2 + (Y - ny / 2) ** 2 + (Z - R - 1) ** 2)
-    d2 = np.sqrt((X - (nx / 2 + R)) ** 2 + (Y - ny / 2) ** 2 + (Z - R - 1) ** 2)
-    phi = -np.tanh(2.0 * (np.minimum(d1, d2) - R) / 4.0)
-    zero = np.zeros(phi.shape)
+    case = wl.DropJumping(0.037)
+    nz, ny, nx = case.shape
     stream = torch.cuda.Stream()
     out = {}
     nodes = nx * ny * nz
     peak, _ = measured_peaks()
+
+    def make(c, prec):
+        return acm.make_params(c.shape, dt=1.0, nu=c.nu, bc=list(c.bc), two_phase=True,
+                               sigma=c.sigma, W=c.W, M=c.M, theta_deg=c.theta_deg, precision=prec)
+
+    init = case.initial()
     for name, prec in (("fp32", acm.FP32_DEV), ("fp64", acm.FP64)):
-        p = acm.make_params((nz, ny, nx), dt=0.5, nu=0.05, bc=[0, 0, 0, 0, 1, 1],
-                            two_phase=True, sigma=1e-2, W=4.0, M=1.0, theta_deg=180.0,
-                            precision=prec)
-        s = acm.Solver(p)
+        s = acm.Solver(make(case, prec))
         s.set_stream(stream.cuda_stream)
-        s.set_fields(np.ones(phi.shape), zero, zero, zero, phi)
+        s.set_fields(*init)
         s.step(max(args.warmup, 64))
         s.sync()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -743,15 +747,50 @@ def run_twophase3d(args):
                      "seconds_for_40_steps": secs / args.steps * 40,
                      "hbm_frac_at_10_words": 10 * es * nodes * args.steps / secs / 1e9 / peak}
         s.close()
+
+    physics = {}
+    if args.tci > 0:
+        runs = [("oh0.037_fp32", 0.037, acm.FP32_DEV), ("oh0.119_fp32", 0.119, acm.FP32_DEV)]
+        if args.tci_fp64:
+            runs.append(("oh0.037_fp64", 0.037, acm.FP64))
+        for key, oh, prec in runs:
+            c = wl.DropJumping(oh)
+            s = acm.Solver(make(c, prec))
+            s.set_stream(stream.cuda_stream)
+            s.set_fields(*c.initial())
+            every = max(1, int(round(c.t_ci / 8)))
+            total = int(round(args.tci * c.t_ci))
+            curve, done, status = [], 0, "ok"
+            t0 = time.perf_counter()
+            while done < total:
+                m = min(every, total - done)
+                try:
+                    s.step(m)
+                    s.sync()
+                except acm.AcmError as e:
+                    status = f"blow-up before step {done + m}: {e}"
+                    break
+                done += m
+                f = s.fields()
+                wd, zc, hb = c.observables(f[3], f[4])
+                curve.append([round(done / c.t_ci, 4), wd, zc, hb])
+            physics[key] = {"steps": done, "t_ci_steps": c.t_ci, "status": status,
+                            "seconds": time.perf_counter() - t0,
+                            "columns": ["t/T_ci", "W_drop/U_ci", "z_c/R", "h_b/R"],
+                            "curve": curve}
+            s.close()
     print(json.dumps({
         "metric": "GLUPS", "value": out["fp32"]["GLUPS"], "unit": "GLUPS", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": out["fp32"]["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "3D two-phase, 120x120x200, two drops on a nonwetting wall "
-                               "(theta=180), D3Q19 isotropic CHE, c=2; five launches per step"},
+        "config": {"workload": "3D two-phase, Section 3.7 drop jumping on the quarter domain "
+                               "120x120x200 (symmetry planes x, y; walls z; theta=180), "
+                               "Oh=0.037, N_L=40, c=10, Cn=0.1, Pe=8e3; D3Q19 isotropic CHE; "
+                               "five launches per step"},
         "runs": out,
-        "paper_context": {"seconds_for_40_steps": 26.0, "hardware": "4 CPU nodes (AMReX)"},
+        "physics": physics,
+        "paper_context": {"seconds_for_40_steps": 26.0, "hardware": "4 CPU nodes"},
     }))
     return 0
 
@@ -873,6 +912,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-check", action="store_true",
                     help="skip the FP64 accuracy run of the tgv3d bench (profiling runs)")
+    ap.add_argument("--tci", type=float, default=0.0,
+                    help="twophase3d: also run the drop-jumping physics to t = TCI T_ci")
+    ap.add_argument("--tci-fp64", action="store_true",
+                    help="twophase3d: add an FP64 run of Oh = 0.037 to the physics runs")
     ap.add_argument("--accuracy-every", type=int, default=0,
                     help="tgv3d: also run FP32 and FP64 side by side from the initial field "
                          "and compare them every this many steps (the FP32-vs-FP64 curve)")

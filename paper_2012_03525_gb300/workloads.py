@@ -237,3 +237,97 @@ def wall_cap(nx: int, ny: int, radius: float, theta_deg: float, W: float = 4.0, 
     X, Y = np.meshgrid(x, y, indexing="xy")
     phi = -np.tanh(2.0 * (np.hypot(X - xc, Y - yc) - radius) / W)
     return np.ones((ny, nx)), np.zeros((ny, nx)), np.zeros((ny, nx)), phi
+
+
+@dataclasses.dataclass
+class DropJumping:
+    """Coalescence-induced drop jumping on a nonwetting wall (Section 3.7):
+    two drops of radius R = N_L centred at (+-R, 0, R) in the box
+    [-3R, 3R]^2 x [0, 5R], theta = 180 degrees, simulated on the quarter
+    [0, 3R]^2 x [0, 5R] with symmetry planes on the x and y faces (3 N_L x
+    3 N_L x 5 N_L nodes) and walls on the z faces.  Re = 1 / Oh^2 (the
+    paper's Re = sigma R / (rho0 nu^2), i.e. U_c = sigma / (rho0 nu) as in
+    Section 3.4), so in lattice units U_c = 1 / c, nu = U_c N_L / Re,
+    sigma = U_c nu, W = Cn N_L, M = U_c N_L^2 / (Pe sigma); results are
+    scaled by the capillary-inertial U_ci = sqrt(sigma / (rho0 R)) and
+    T_ci = R / U_ci."""
+    oh: float
+    n_l: int = 40
+    c: float = 10.0
+    cn: float = 0.1
+    pe: float = 8e3
+
+    @property
+    def u_c(self):
+        return 1.0 / self.c
+
+    @property
+    def re(self):
+        return 1.0 / self.oh ** 2
+
+    @property
+    def nu(self):
+        return self.u_c * self.n_l / self.re
+
+    @property
+    def sigma(self):
+        return self.u_c * self.nu
+
+    @property
+    def W(self):
+        return self.cn * self.n_l
+
+    @property
+    def M(self):
+        return self.u_c * self.n_l ** 2 / (self.pe * self.sigma)
+
+    @property
+    def u_ci(self):
+        return float(np.sqrt(self.sigma / self.n_l))
+
+    @property
+    def t_ci(self):
+        return self.n_l / self.u_ci
+
+    @property
+    def shape(self):
+        return (5 * self.n_l, 3 * self.n_l, 3 * self.n_l)
+
+    bc = (4, 4, 4, 4, 1, 1)  # symmetry x, y faces; walls z
+    theta_deg = 180.0
+
+    def initial(self):
+        """phi = -tanh(2 (r - R) / W), r the distance to the drop centre
+        (R, 0, R) (its mirror image across x = 0 is the second drop), fluid at
+        rest, rho = 1."""
+        nz, ny, nx = self.shape
+        R = float(self.n_l)
+        Z, Y, X = np.meshgrid(np.arange(nz, dtype=np.float64), np.arange(ny, dtype=np.float64),
+                              np.arange(nx, dtype=np.float64), indexing="ij")
+        r = np.sqrt((X - R) ** 2 + Y ** 2 + (Z - R) ** 2)
+        phi = -np.tanh(2.0 * (r - R) / self.W)
+        z = np.zeros(self.shape)
+        return np.ones(self.shape), z, z.copy(), z.copy(), phi
+
+    def observables(self, w, phi):
+        """Drop centroid velocity W_drop / U_ci and height z_c / R (weights
+        (1 + phi) / 2), and the height h_b / R of the drop's lowest point: the
+        lowest crossing of phi = 0 over all x-y columns, linearly
+        interpolated (0 while the drop touches the wall plane)."""
+        nz = phi.shape[0]
+        wt = 0.5 * (1.0 + phi)
+        zs = np.arange(nz, dtype=np.float64)[:, None, None]
+        wd = float((w * wt).sum() / wt.sum())
+        zc = float((zs * wt).sum() / wt.sum())
+        pos = phi > 0
+        has = pos.any(axis=0)
+        k = np.argmax(pos, axis=0)[has]
+        if k.size == 0:
+            hb = float("nan")
+        else:
+            cols = np.nonzero(has)
+            f1 = phi[k, cols[0], cols[1]]
+            f0 = phi[np.maximum(k - 1, 0), cols[0], cols[1]]
+            zb = np.where(k > 0, (k - 1) + (-f0) / (f1 - f0 + 1e-300), 0.0)
+            hb = float(zb.min())
+        return wd / self.u_ci, zc / self.n_l, hb / self.n_l

@@ -270,3 +270,36 @@ def test_symmetry_planes_equal_doubled_box_on_gpu():
         f = s.fields()
     for k in range(5):
         assert np.abs(q[k] - f[k][:, :ny, :nx]).max() < 1e-13, k
+
+
+def _jump_curve(case, prec, quarters):
+    p = acm.make_params(case.shape, dt=1.0, nu=case.nu, bc=list(case.bc), two_phase=True,
+                        sigma=case.sigma, W=case.W, M=case.M, theta_deg=case.theta_deg,
+                        precision=prec)
+    every = int(case.t_ci / 4)
+    out = []
+    with acm.Solver(p) as s:
+        s.set_fields(*case.initial())
+        for _ in range(quarters):
+            s.step(every)
+            s.sync()  # raises on a blow-up
+            f = s.fields()
+            out.append(case.observables(f[3], f[4]))
+    return np.array(out)
+
+
+def test_drop_jumping_quarter_domain_section_3_7():
+    """Section 3.7's coalescence-induced jumping on the quarter domain with
+    symmetry planes (reduced to N_L = 16, W = 4 nodes; Oh = 0.037, c = 10,
+    Pe = 8e3, theta = 180): the run is stable for 4 T_ci, the coalesced drop
+    pushes off the nonwetting wall (W_drop > 0 after coalescence) and its
+    centroid rises, and FP32 deviation storage follows FP64."""
+    from paper_2012_03525_gb300 import workloads as wl
+    case = wl.DropJumping(0.037, n_l=16, cn=0.25)
+    c64 = _jump_curve(case, acm.FP64, 16)
+    c32 = _jump_curve(case, acm.FP32_DEV, 16)
+    wd, zc = c64[:, 0], c64[:, 1]
+    assert np.all(wd[4:] > 0)          # upward centroid velocity from t = 1.25 T_ci on
+    assert zc[-1] > 1.15 and np.all(np.diff(zc[3:]) > 0)
+    assert np.abs(c32[:, 0] - wd).max() < 2e-3
+    assert np.abs(c32[:, 1] - zc).max() < 2e-3
