@@ -423,8 +423,12 @@ def run_closure(args):
         256^2 (FP32) and 512^2 (FP64);
       * free rollouts to fixed physical times (the C5 curve): velocity error
         after every window and wall time of the whole run for plain 256^2
-        FP32/FP64, plain 512^2 FP64, the corrected 256^2 FP32 run (full and
-        damped correction), and the 1024^2 FP64 reference's own time."""
+        FP32/FP64, plain 512^2 FP64, the corrected 256^2 FP32 run (closure
+        trained with pushforward rounds; full and damped correction; and the
+        closure trained on one-window samples only), and the 1024^2 FP64
+        reference's own time;
+      * time to eps: how many windows each free run stays within eps of the
+        reference, and the wall time that takes."""
     import numpy as np
     import torch
     from paper_2012_03525_gb300 import acm, build
@@ -435,22 +439,29 @@ def run_closure(args):
     B = 4
     train_seeds = list(wl.TURB_TRAIN_SEEDS)[:args.train_trajectories]
     test_seeds = list(wl.TURB_TEST_SEEDS)[:B]
+    # one-window training only (the earlier recipe): good one-window error,
+    # but the corrected free run diverges
     t0 = time.perf_counter()
     X, Y = cl.generate(setup, train_seeds, 12, torch, B, reset=True)
-    t_gen = time.perf_counter() - t0
+    clo0, _ = cl.train(setup, X, Y, torch, B, epochs=20, lr=1e-3)
+    del X, Y
+    curve0 = cl.rollout_curve(setup, clo0, test_seeds, 12, torch, B)["closure_coarse_fp32"]
+    clo0.close()
+    # pushforward training: the same first round, then rounds on the states
+    # the corrected runs reach
     t0 = time.perf_counter()
-    clo, losses = cl.train(setup, X, Y, torch, B, epochs=20, lr=1e-3)
+    clo, hist = cl.fit_pushforward(setup, train_seeds, 12, torch, B)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
-    del X, Y
+    losses = [h for r in hist for h in r]
     ew = cl.evaluate_windows(setup, clo, test_seeds, 6, torch, B)
     curve = cl.rollout_curve(setup, clo, test_seeds, 12, torch, B)
-    # the same closure with its correction scaled by 1/4 (the output layer is
+    # the same closure with its correction scaled by 3/4 (the output layer is
     # linear): a damped correction
     w_full = clo.get_weights()
     nlast = 3 * 32 * 9 + 3
     w_damp = w_full.copy()
-    w_damp[-nlast:] *= 0.25
+    w_damp[-nlast:] *= 0.75
     clo.set_weights(w_damp)
     curve_damped = cl.rollout_curve(setup, clo, test_seeds, 12, torch, B)["closure_coarse_fp32"]
     clo.set_weights(w_full)
@@ -514,9 +525,24 @@ def run_closure(args):
 
     horizon = {k: {"final_error": v["final_error"], "seconds": v["seconds"],
                    "error_per_window": v.get("error_per_window")} for k, v in curve.items()}
-    horizon["closure_coarse_fp32_damped_0.25"] = {
+    horizon["closure_coarse_fp32_damped_0.75"] = {
         "final_error": curve_damped["final_error"], "seconds": curve_damped["seconds"],
         "error_per_window": curve_damped["error_per_window"]}
+    horizon["closure_coarse_fp32_one_window_training_only"] = {
+        "final_error": curve0["final_error"], "seconds": curve0["seconds"],
+        "error_per_window": curve0["error_per_window"]}
+
+    # time to eps: windows (x window x dt) before the free run's error first
+    # exceeds eps, and the wall time of that many windows
+    def time_to(errs, secs, eps):
+        k = 0
+        while k < len(errs) and errs[k] <= eps:
+            k += 1
+        return {"windows": k, "physical_time": k * setup.window * setup.dt,
+                "seconds": secs * k / 12}
+    tte = {f"eps_{eps}": {name: time_to(v["error_per_window"], v["seconds"], eps)
+                          for name, v in horizon.items() if v.get("error_per_window")}
+           for eps in (0.01, 0.02, 0.03, 0.04)}
     res = {
         "metric": "time-to-eps (one-window velocity error vs filtered 1024^2 FP64 reference)",
         "value": t_cc, "unit": "s per window (4 runs)", "n_gpus": 1, "higher_is_better": False,
@@ -526,13 +552,17 @@ def run_closure(args):
                    "train_trajectories": len(train_seeds), "windows_per_trajectory": 12,
                    "test_trajectories": len(test_seeds)},
         "train": {"loss_first_epoch": losses[0], "loss_last_epoch": losses[-1],
-                  "generate_s": t_gen, "train_s": t_train},
+                  "recipe": "one-window samples, then pushforward rounds (restart every r "
+                            "windows, closure applied in between) r = "
+                            + ", ".join(str(r) for r, _, _ in cl.PUSHFORWARD_SCHEDULE),
+                  "generate_and_train_s": t_train},
         "one_window_error": {"coarse256_fp32": ew["plain"], "coarse256_fp32_closure": ew["closure"],
                              "plain512_fp64": float(np.mean(errs))},
         "seconds_per_window": {"coarse256_fp32": t_c, "coarse256_fp32_closure": t_cc,
                                "closure_apply": t_apply, "plain512_fp64": t_m,
                                "plain1024_fp64": t_f},
         "rollout_12_windows": {"physical_time": 12 * setup.window * setup.dt, "runs": horizon},
+        "time_to_eps": tte,
         "per_step_closure": {"one_step_error": {"coarse256_fp32": ew1["plain"],
                                                 "coarse256_fp32_closure": ew1["closure"]},
                              "seconds_per_coarse_step": t_step,

@@ -70,15 +70,19 @@ def _fine(setup, seeds, n=None, precision=acm.FP64):
     return s
 
 
-def generate(setup, seeds, windows, torch, batch, model=None, reset=False):
+def generate(setup, seeds, windows, torch, batch, model=None, reset=False, reset_every=0):
     """Training samples, (X, Y) device tensors [nsamples][batch][3][nc][nc]
     (normalised): inputs are coarse states after each window, targets the
     filtered fine states at the same times.  The coarse run starts from the
     filtered fine state and then runs freely (with ``reset`` it restarts from
-    the filtered fine state every window instead).  With a trained ``model``
-    the closure is applied after every window, so the inputs are the states
-    the closure meets in use (the data-aggregation remedy for the drift of a
-    corrected run away from the training states)."""
+    the filtered fine state every window instead; with ``reset_every`` = r > 0
+    every r windows).  With a trained ``model`` the closure is applied after
+    every window, so the inputs are the states the closure meets in use (the
+    data-aggregation remedy for the drift of a corrected run away from the
+    training states; with a small r the drift is the model's own over r - 1
+    corrected windows)."""
+    if reset:
+        reset_every = 1
     nc = setup.n_coarse
     sr, su = setup.scales()
     closure = model
@@ -93,8 +97,8 @@ def generate(setup, seeds, windows, torch, batch, model=None, reset=False):
         fine = _fine(setup, group)
         coarse = acm.Solver([setup.params(nc, acm.FP32_DEV) for _ in group])
         fine.restrict_to(coarse, setup.factor)
-        for _ in range(windows):
-            if reset:
+        for k in range(windows):
+            if reset_every > 0 and k % reset_every == 0:
                 fine.restrict_to(coarse, setup.factor)
             coarse.step(setup.window)
             fine.step(setup.window)
@@ -205,6 +209,38 @@ def fit(setup, train_seeds, windows, torch, batch, epochs=20, lr=1e-3, rounds=2,
         Y = torch.cat([Y, Y2])
         closure, losses = train(setup, X, Y, torch, batch, epochs, lr * 0.5, seed, closure)
         hist.append(losses)
+    return closure, hist
+
+
+# (restart interval in windows, epochs, learning rate) of each aggregation round
+PUSHFORWARD_SCHEDULE = ((2, 10, 5e-4), (3, 10, 5e-4), (4, 10, 5e-4), (6, 10, 2.5e-4),
+                        (8, 10, 2.5e-4), (12, 10, 2.5e-4))
+
+
+def fit_pushforward(setup, train_seeds, windows, torch, batch, schedule=PUSHFORWARD_SCHEDULE,
+                    epochs=20, lr=1e-3, seed=0):
+    """Train on one-window samples (every window restarted from the filtered
+    fine state), then for each (r, epochs, lr) of ``schedule`` add samples
+    from coarse runs corrected by the current closure and restarted from the
+    filtered fine state every r windows, and continue training on all
+    samples.  Each round teaches the closure to pull back the drift that its
+    own corrections leave over r - 1 windows (its inputs are the states it
+    meets in use, its targets the filtered fine states at the same times), so
+    the corrected free run stays near the reference for longer; with
+    one-window samples only, the corrected run drifts off after 3-4 windows
+    and diverges.  Returns (closure, per-round loss histories)."""
+    X, Y = generate(setup, train_seeds, windows, torch, batch, reset=True)
+    closure, losses = train(setup, X, Y, torch, batch, epochs, lr, seed)
+    hist = [losses]
+    for r_every, ep, lr_r in schedule:
+        X2, Y2 = generate(setup, train_seeds, windows, torch, batch, model=closure,
+                          reset_every=r_every)
+        X = torch.cat([X, X2])
+        Y = torch.cat([Y, Y2])
+        del X2, Y2
+        closure, losses = train(setup, X, Y, torch, batch, ep, lr_r, seed, closure)
+        hist.append(losses)
+    del X, Y
     return closure, hist
 
 

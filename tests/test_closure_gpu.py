@@ -169,3 +169,27 @@ def test_input_noise_is_seeded_and_off_by_default(torch):
         lc, _ = c.loss_grad(xd.data_ptr(), td.data_ptr())
     assert l1 == l0
     assert la == lb and la != l0 and lc != la
+
+
+def test_pushforward_samples_restart_every_r_windows(torch):
+    """Data aggregation with restarts (closure.generate, reset_every = r):
+    the windows that start from the filtered fine state give exactly the
+    one-window samples; the windows in between start from the corrected
+    state, so they differ; targets are the filtered fine states throughout."""
+    from paper_2012_03525_gb300 import closure as cl
+    setup = cl.Setup(n_fine=128, factor=4, window=4)
+    seeds, B = [0, 1], 2
+    X1, Y1 = cl.generate(setup, seeds, 4, torch, B, reset=True)
+    clo = acm.Closure(setup.n_coarse, setup.n_coarse, B)
+    clo.set_scales(*setup.scales())
+    w = cl.he_init(0, scale_out=1.0)  # a correction large enough to matter
+    clo.set_weights(w)
+    X2, Y2 = cl.generate(setup, seeds, 4, torch, B, model=clo, reset_every=2)
+    torch.cuda.synchronize()
+    assert X2.shape == X1.shape
+    assert torch.equal(Y1, Y2)
+    for k in (0, 2):
+        assert torch.equal(X1[k], X2[k])
+    for k in (1, 3):
+        assert not torch.equal(X1[k], X2[k])
+    clo.close()
