@@ -698,6 +698,13 @@ def run_mames(args):
         out[name]["tgv4096_fp32_GLUPS"] = n2 * n2 * args.steps / secs / 1e9
         out[name]["tgv4096_fp32_hbm_frac"] = (24 * n2 * n2 * args.steps / secs / 1e9 /
                                               measured_peaks()[0])
+        if sc == acm.SCHEME_SMAMES:
+            # the same step on the general tile kernel (the line-marching
+            # kernel is the default for this periodic grid)
+            s.set_tuning(acm.TUNE_LINE2D, 0)
+            s.step(16)
+            secs_t = timed(s, args.steps)
+            out[name]["tgv4096_fp32_GLUPS_tile_kernel"] = n2 * n2 * args.steps / secs_t / 1e9
         s.close()
     # (c) Section 3.1 accuracy
     n3, c = 100, 20.0

@@ -285,7 +285,11 @@ enum {
     ACM_TUNE_ZCHUNKS = 1,     /* 3D: z-chunks per x-y column (>= 1; 0 = chunks of 16 planes) */
     ACM_TUNE_T3Y = 2,         /* 3D: tile height in y, 8 or 16 */
     ACM_TUNE_GRAPH_STEPS = 3, /* steps per captured CUDA graph, even, >= 2; 0 disables graphs */
-    ACM_TUNE_BLOCKS = 4       /* 2D: persistent CTAs per launch (0 = fill the GPU) */
+    ACM_TUNE_BLOCKS = 4,      /* 2D: persistent CTAs per launch (0 = fill the GPU) */
+    ACM_TUNE_LINE2D = 5       /* 2D single-phase runs periodic on all faces with a width
+                                 that is a multiple of 64: 1 steps them with the
+                                 line-marching kernel (the default for FP32_DEV storage),
+                                 0 with the tile kernel (the default for FP64) */
 };
 acm_status acm_set_tuning(acm_handle *h, int key, int value);
 
@@ -293,7 +297,8 @@ acm_status acm_set_tuning(acm_handle *h, int key, int value);
 int acm_get_tuning(const acm_handle *h, int key);
 
 /* Autotuner: time NSTEPS steps of every candidate launch shape (3D: tile
- * height x z-chunking; 2D: persistent CTA count) with CUDA events on the
+ * height x z-chunking; 2D: persistent CTA count of the tile kernel and,
+ * where it applies, the line-marching kernel) with CUDA events on the
  * handle's stream, keep the fastest (readable with acm_get_tuning) and
  * restore the fields as they were (trial steps run on a device copy, which
  * this call allocates and frees).  *best_ms_per_step receives the winner's

@@ -16,7 +16,7 @@ OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5, 
 BC_PERIODIC, BC_WALL, BC_LID, BC_HALO, BC_SYMMETRY = 0, 1, 2, 3, 4
 FP64, FP32_DEV = 0, 1
 SCHEME_SMAMES, SCHEME_MAMES = 0, 1
-TUNE_ZCHUNKS, TUNE_T3Y, TUNE_GRAPH_STEPS, TUNE_BLOCKS = 1, 2, 3, 4
+TUNE_ZCHUNKS, TUNE_T3Y, TUNE_GRAPH_STEPS, TUNE_BLOCKS, TUNE_LINE2D = 1, 2, 3, 4, 5
 
 #: every symbol include/acm.h declares (checked by the CPU tests)
 EXPORTS = ["acm_create", "acm_batch_create", "acm_set_stream", "acm_nruns", "acm_set_fields",

@@ -35,6 +35,9 @@ struct acm_handle {
     RunDesc *druns = nullptr;
     int4 *dwork = nullptr;
     int nwork = 0;
+    int4 *dline = nullptr;            // 2D line-marching work list (empty if it does not apply)
+    int nline = 0;
+    bool line_gen = false;            // some run has rho0 != 1 or a body force
     size_t pool = 0;                  // elements per field pool
     void *buf[2][NFIELD] = {};
     int cur = 0;
@@ -291,6 +294,7 @@ void release(acm_handle *h)
                 if (h->buf[b][f]) cudaFree(h->buf[b][f]);
     if (h->druns) cudaFree(h->druns);
     if (h->dwork) cudaFree(h->dwork);
+    if (h->dline) cudaFree(h->dline);
     if (h->derr) cudaFree(h->derr);
     if (h->dpartials) cudaFree(h->dpartials);
     if (h->dout) cudaFree(h->dout);
@@ -404,6 +408,39 @@ acm_status create_common(const acm_params *params, int nruns, acm_handle **out,
     }
     h->pool = off;
     h->nwork = (int)work.size();
+    // the line-marching kernel covers single-phase 2D runs that are periodic
+    // on all four faces, with a width that is a multiple of its strip
+    std::vector<int4> line;
+    if (h->dim == 2 && !h->two_phase) {
+        bool ok = true;
+        for (const RunDesc &d : h->runs) {
+            for (int f = 0; f < 4; ++f) ok &= d.bc[f] == ACM_BC_PERIODIC;
+            ok &= d.nx % line2d_width() == 0 && d.ny >= 4;
+            h->line_gen |= d.rho0 != 1.0 || d.g[0] != 0.0 || d.g[1] != 0.0;
+        }
+        // rows per item: the most (up to line2d_rows()) that still give 32
+        // items per SM (two per warp slot at 16 resident warps); short items
+        // (down to 4 rows) spread small grids over the GPU
+        int rows = line2d_rows();
+        auto count = [&](int rr) {
+            long long n = 0;
+            for (const RunDesc &d : h->runs)
+                n += (long long)(d.nx / line2d_width()) * ((d.ny + rr - 1) / rr);
+            return n;
+        };
+        while (ok && rows > 4 && count(rows) < 32LL * h->sms) rows /= 2;
+        for (int r = 0; ok && r < nruns; ++r) {
+            const RunDesc &d = h->runs[r];
+            for (int y0 = 0; y0 < d.ny; y0 += rows)
+                for (int x0 = 0; x0 < d.nx; x0 += line2d_width())
+                    line.push_back(make_int4(r, x0, y0, std::min(rows, d.ny - y0)));
+        }
+    }
+    h->nline = (int)line.size();
+    // the line-marching kernel is the default for FP32 storage; in FP64 its
+    // register queue limits it to one CTA per SM and the tile kernel is
+    // faster on the grids measured
+    h->tune.line2d = h->prec == ACM_FP64 ? 0 : 1;
 
 #define CKB(call)                                    \
     do {                                             \
@@ -456,6 +493,10 @@ acm_status create_common(const acm_params *params, int nruns, acm_handle **out,
         CKB(cudaMalloc(&h->dwork, sizeof(int4) * work.size()));
         CKB(cudaMemcpy(h->dwork, work.data(), sizeof(int4) * work.size(), cudaMemcpyHostToDevice));
     }
+    if (!line.empty()) {
+        CKB(cudaMalloc(&h->dline, sizeof(int4) * line.size()));
+        CKB(cudaMemcpy(h->dline, line.data(), sizeof(int4) * line.size(), cudaMemcpyHostToDevice));
+    }
     CKB(cudaMalloc(&h->derr, sizeof(unsigned)));
     CKB(cudaMemset(h->derr, 0, sizeof(unsigned)));
     const long long per_run_blocks = (maxn + 255) / 256;
@@ -472,6 +513,10 @@ acm_status create_common(const acm_params *params, int nruns, acm_handle **out,
     if (h->dim == 2) {
         if (h->prec == ACM_FP64) step2d_max_blocks_per_sm<double>(h->two_phase);
         else step2d_max_blocks_per_sm<float>(h->two_phase);
+        if (h->nline > 0) {
+            if (h->prec == ACM_FP64) line2d_prepare<double>();
+            else line2d_prepare<float>();
+        }
         if (h->scheme == ACM_SCHEME_MAMES) {
             if (h->prec == ACM_FP64) mames2d_max_blocks_per_sm<double>();
             else mames2d_max_blocks_per_sm<float>();
@@ -535,6 +580,9 @@ cudaError_t one_step(acm_handle *h, int from)
         return launch_mames2d<T>(h->druns, h->dwork, h->nwork, in, out, h->derr, blocks,
                                  h->stream);
     }
+    if (h->nline > 0 && h->tune.line2d)
+        return launch_line2d<T>(h->druns, h->dline, h->nline, h->line_gen, in, out, h->derr,
+                                h->stream);
     if (blocks <= 0) blocks = h->sms * step2d_max_blocks_per_sm<T>(h->two_phase);
     return launch_step2d<T>(h->druns, h->dwork, h->nwork, h->two_phase, in, out, h->derr, blocks,
                             h->stream);
@@ -766,6 +814,10 @@ acm_status acm_set_tuning(acm_handle *h, int key, int value)
         if (value < 0) return fail(h, ACM_EINVAL, "blocks must be >= 0");
         h->tune.blocks = value;
         break;
+    case ACM_TUNE_LINE2D:
+        if (value != 0 && value != 1) return fail(h, ACM_EINVAL, "line2d must be 0 or 1");
+        h->tune.line2d = value;
+        break;
     default:
         return fail(h, ACM_EINVAL, "unknown tuning key");
     }
@@ -781,6 +833,7 @@ int acm_get_tuning(const acm_handle *h, int key)
     case ACM_TUNE_T3Y: return h->tune.t3y;
     case ACM_TUNE_GRAPH_STEPS: return h->tune.graph_steps;
     case ACM_TUNE_BLOCKS: return h->tune.blocks;
+    case ACM_TUNE_LINE2D: return h->tune.line2d;
     default: return -1;
     }
 }
@@ -797,7 +850,7 @@ acm_status acm_autotune(acm_handle *h, int nsteps, double *best_ms_per_step)
     CK(h, cudaStreamSynchronize(h->stream));
 
     // candidate launch shapes
-    struct Cand { int t3y, zchunks, blocks; };
+    struct Cand { int t3y, zchunks, blocks, line2d; };
     std::vector<Cand> cands;
     if (h->dim == 3) {
         const int nz = h->runs[0].nz;
@@ -806,7 +859,7 @@ acm_status acm_autotune(acm_handle *h, int nsteps, double *best_ms_per_step)
             for (int zc : zc_opts) {
                 bool dup = false;
                 for (const Cand &c : cands) dup |= (c.t3y == t3y && c.zchunks == zc);
-                if (!dup) cands.push_back({t3y, zc, 0});
+                if (!dup) cands.push_back({t3y, zc, 0, 0});
             }
     } else {
         const bool mames = h->scheme == ACM_SCHEME_MAMES;
@@ -816,7 +869,8 @@ acm_status acm_autotune(acm_handle *h, int nsteps, double *best_ms_per_step)
                          : step2d_max_blocks_per_sm<double>(h->two_phase))
                 : (mames ? mames2d_max_blocks_per_sm<float>()
                          : step2d_max_blocks_per_sm<float>(h->two_phase));
-        for (int k = 1; k <= per_sm; ++k) cands.push_back({h->tune.t3y, 0, k * h->sms});
+        for (int k = 1; k <= per_sm; ++k) cands.push_back({h->tune.t3y, 0, k * h->sms, 0});
+        if (h->nline > 0 && !mames) cands.push_back({h->tune.t3y, 0, 0, 1});
     }
 
     // keep the state: trial steps run on a copy
@@ -835,7 +889,7 @@ acm_status acm_autotune(acm_handle *h, int nsteps, double *best_ms_per_step)
     const Tuning keep = h->tune;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     double best = 1e300;
-    Cand bestc = {keep.t3y, keep.zchunks, keep.blocks};
+    Cand bestc = {keep.t3y, keep.zchunks, keep.blocks, keep.line2d};
     if (st == ACM_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
         st = fail(h, ACM_ECUDA, "cudaEventCreate failed");
     for (size_t i = 0; i < cands.size() && st == ACM_OK; ++i) {
@@ -849,6 +903,7 @@ acm_status acm_autotune(acm_handle *h, int nsteps, double *best_ms_per_step)
         }
         h->tune.zchunks = c.zchunks;
         h->tune.blocks = c.blocks;
+        h->tune.line2d = c.line2d;
         cudaError_t e = cudaSuccess;
         for (int k = 0; k < 2 && e == cudaSuccess; ++k) {  // warm-up
             e = step_once(h, h->cur);
@@ -891,6 +946,7 @@ acm_status acm_autotune(acm_handle *h, int nsteps, double *best_ms_per_step)
     if (st == ACM_OK) {
         h->tune.zchunks = bestc.zchunks;
         h->tune.blocks = bestc.blocks;
+        h->tune.line2d = bestc.line2d;
         if (h->dim == 3) h->tune.t3y = bestc.t3y;
     }
     if (h->dim == 3 && build_maps(h) != ACM_OK && st == ACM_OK) st = ACM_ECUDA;

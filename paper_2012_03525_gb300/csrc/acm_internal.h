@@ -88,6 +88,7 @@ struct Tuning {
     int t3y = 16;          // 3D: tile height (8 or 16)
     int graph_steps = 64;  // steps per captured CUDA graph (even)
     int blocks = 0;        // 2D: persistent CTAs (0 = occupancy x SMs)
+    int line2d = 1;        // 2D single-phase periodic: line-marching kernel where it applies
 };
 
 // Launchers (defined in the kernel translation units).
@@ -97,6 +98,17 @@ cudaError_t launch_step2d(const RunDesc *druns, const int4 *dwork, int nwork, in
                           cudaStream_t s);
 template <typename T>
 int step2d_max_blocks_per_sm(int two_phase);
+
+// 2D single-phase periodic runs whose width is a multiple of line2d_width():
+// one warp per (run, x0, y0, rows) item of a strip of line2d_width() columns
+// and at most line2d_rows() rows.
+int line2d_rows();
+int line2d_width();
+template <typename T>
+void line2d_prepare();  // launch attributes (before any capture)
+template <typename T>
+cudaError_t launch_line2d(const RunDesc *druns, const int4 *dwork, int nwork, bool gen,
+                          Fields<T> in, Fields<T> out, unsigned *derr, cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_step3d(const CUtensorMap *maps_in, Fields<T> out, const RunDesc &run,

@@ -33,6 +33,7 @@ def sms():
 def _gpu(params, states, steps, blocks):
     with acm.Solver(params) as s:
         s.set_tuning(acm.TUNE_BLOCKS, blocks)
+        s.set_tuning(acm.TUNE_LINE2D, 0)  # the tile kernel's persistent path
         for r, st in enumerate(states):
             s.set_fields(st[0], st[1], st[2], None, st[3] if len(st) > 3 else None, run=r)
         s.step(steps)
