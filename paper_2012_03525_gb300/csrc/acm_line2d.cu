@@ -137,12 +137,11 @@ struct K2 {
     P2<T> rho0, hdt, nhdt, hdtcs2, nhdtcs2, nudt, hsatm, nhsatm, m4, satc, dt, gx, gy;
 };
 
-// one row of the strip: the lane's own pair and its edge pair (meaningful in
-// lanes 0 and 31 only)
+// one row of the strip: the lane's own pair (the edge pairs stay in the
+// ring and are read where they are used)
 template <typename T>
 struct Row {
-    P2<T> r, u, v;     // own pair
-    P2<T> hr, hu, hv;  // edge pair: lane 0 west (x0-2, x0-1), lane 31 east (x0+64, x0+65)
+    P2<T> r, u, v;
 };
 
 // x-neighbours of the own pair from the adjacent lanes: W = (west of a, a),
@@ -271,34 +270,37 @@ __global__ void __launch_bounds__(32 * LWARPS, sizeof(T) == 4 ? LMINB : 1)
         }
         cp_async_commit();
     };
-    // read row y from its slot (its group has completed)
+    // read row y's own pair from its slot (its group has completed)
     auto read_row = [&](int y, Row<T> &q) {
         const int k = (y - y0 + 2) & (LRING - 1);
         q.r = *reinterpret_cast<const P2<T> *>(own_slot + (k * 3 + 0) * 64);
         q.u = *reinterpret_cast<const P2<T> *>(own_slot + (k * 3 + 1) * 64);
         q.v = *reinterpret_cast<const P2<T> *>(own_slot + (k * 3 + 2) * 64);
-        if (edge) {
-            q.hr = *reinterpret_cast<const P2<T> *>(edge_slot + (k * 3 + 0) * 4);
-            q.hu = *reinterpret_cast<const P2<T> *>(edge_slot + (k * 3 + 1) * 4);
-            q.hv = *reinterpret_cast<const P2<T> *>(edge_slot + (k * 3 + 2) * 4);
-        } else {
-            q.hr = q.hu = q.hv = splat(T(0));
-        }
     };
-    // Eq. (2.10) on row 1 of (q0, q1, q2) = rows (y-1, y, y+1): the own pair
+    // edge pair of field f of row y (meaningful in lanes 0 and 31; the other
+    // lanes read lane 0's slot and ignore it)
+    auto edge_of = [&](int y, int f) {
+        const int k = (y - y0 + 2) & (LRING - 1);
+        return *reinterpret_cast<const P2<T> *>(edge_slot + (k * 3 + f) * 4);
+    };
+    // Eq. (2.10) on row y of (q0, q1, q2) = rows (y-1, y, y+1): the own pair
     // into d, the edge lanes' outside node into dh
-    auto delta_row = [&](const Row<T> &q0, const Row<T> &q1, const Row<T> &q2, P2<T> &d, T &dh) {
+    auto delta_row = [&](int y, const Row<T> &q0, const Row<T> &q1, const Row<T> &q2, P2<T> &d,
+                         T &dh) {
+        const P2<T> h1r = edge_of(y, 0), h1u = edge_of(y, 1);
         P2<T> rW, rE, uW, uE;
-        neighbours<T>(q1.r, q1.hr, lane, rW, rE);
-        neighbours<T>(q1.u, q1.hu, lane, uW, uE);
+        neighbours<T>(q1.r, h1r, lane, rW, rE);
+        neighbours<T>(q1.u, h1u, lane, uW, uE);
         d = delta2<GEN, T>(K, q1.r, rE, rW, q2.r, q0.r, uE, uW, q2.v, q0.v);
         // outside node: lane 0 at x0-1 (W x0-2, E x0), lane 31 at x0+64
         // (W x0+63, E x0+65); N and S from the edge pairs of rows y+1, y-1
-        const T c = L0 ? q1.hr.y : q1.hr.x;
-        const T e = L0 ? q1.r.x : q1.hr.y, w = L0 ? q1.hr.x : q1.r.y;
-        const T ue = L0 ? q1.u.x : q1.hu.y, uw = L0 ? q1.hu.x : q1.u.y;
-        const T n = L0 ? q2.hr.y : q2.hr.x, s = L0 ? q0.hr.y : q0.hr.x;
-        const T vn = L0 ? q2.hv.y : q2.hv.x, vs = L0 ? q0.hv.y : q0.hv.x;
+        const P2<T> h2r = edge_of(y + 1, 0), h0r = edge_of(y - 1, 0);
+        const P2<T> h2v = edge_of(y + 1, 2), h0v = edge_of(y - 1, 2);
+        const T c = L0 ? h1r.y : h1r.x;
+        const T e = L0 ? q1.r.x : h1r.y, w = L0 ? h1r.x : q1.r.y;
+        const T ue = L0 ? q1.u.x : h1u.y, uw = L0 ? h1u.x : q1.u.y;
+        const T n = L0 ? h2r.y : h2r.x, s = L0 ? h0r.y : h0r.x;
+        const T vn = L0 ? h2v.y : h2v.x, vs = L0 ? h0v.y : h0v.x;
         dh = delta1<GEN, T>(K, c, e, w, n, s, ue, uw, vn, vs);
     };
 
@@ -313,8 +315,8 @@ __global__ void __launch_bounds__(32 * LWARPS, sizeof(T) == 4 ? LMINB : 1)
     read_row(y0 - 1, Q[1]);
     read_row(y0, Q[2]);
     read_row(y0 + 1, Q[3]);
-    delta_row(Q[0], Q[1], Q[2], D[1], DH[1]);
-    delta_row(Q[1], Q[2], Q[3], D[2], DH[2]);
+    delta_row(y0 - 1, Q[0], Q[1], Q[2], D[1], DH[1]);
+    delta_row(y0, Q[1], Q[2], Q[3], D[2], DH[2]);
 
     T *orr = out.f[F_R] + R.off, *ou = out.f[F_U] + R.off, *ov = out.f[F_V] + R.off;
     P2<T> acc = splat(T(0));
@@ -331,14 +333,14 @@ __global__ void __launch_bounds__(32 * LWARPS, sizeof(T) == 4 ? LMINB : 1)
         cp_async_wait<LAHEAD - 3>();
         read_row(y + 2, Q[S2]);
         issue_row(y + LAHEAD);
-        delta_row(Q[S0], Q[S1], Q[S2], D[S1], DH[S1]);
+        delta_row(y + 1, Q[S0], Q[S1], Q[S2], D[S1], DH[S1]);
 
         // Eq. (2.11) on row y
         const Row<T> &c = Q[S0], &n = Q[S1], &s = Q[SM];
         P2<T> rW, rE, uW, uE, vW, vE, dW, dE;
-        neighbours<T>(c.r, c.hr, lane, rW, rE);
-        neighbours<T>(c.u, c.hu, lane, uW, uE);
-        neighbours<T>(c.v, c.hv, lane, vW, vE);
+        neighbours<T>(c.r, edge_of(y, 0), lane, rW, rE);
+        neighbours<T>(c.u, edge_of(y, 1), lane, uW, uE);
+        neighbours<T>(c.v, edge_of(y, 2), lane, vW, vE);
         {
             const P2<T> d0 = D[S0];
             const T up = __shfl_up_sync(FULL, d0.y, 1);
@@ -413,6 +415,12 @@ void line2d_prepare()
     const int smem = (int)(LWARPS * RING_ELEMS * sizeof(T));
     cudaFuncSetAttribute(k_line2d<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     cudaFuncSetAttribute(k_line2d<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+#ifdef ACM_LINE2D_CARVE
+    cudaFuncSetAttribute(k_line2d<T, true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         ACM_LINE2D_CARVE);
+    cudaFuncSetAttribute(k_line2d<T, false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         ACM_LINE2D_CARVE);
+#endif
 }
 
 template <typename T>
