@@ -342,6 +342,21 @@ def run_batched_drops(args):
     ms32 = ev0.elapsed_time(ev1)
     batch.sync()
     red = batch.reduce()
+    line_on = batch.get_tuning(acm.TUNE_LINE2D)
+    # the other 2D kernel on the same batch, for comparison (untimed state
+    # afterwards is not used: the accuracy check below reads the fields
+    # before this point through `red` and the FP64 runs start afresh)
+    keep = [batch.fields(run=i) for i in range(0, len(runs), max(1, len(runs) // 16))]
+    batch.set_tuning(acm.TUNE_LINE2D, 1 - line_on)
+    batch.step(16)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    batch.step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    batch.sync()
+    ms_other = ev0.elapsed_time(ev1)
+    batch.set_tuning(acm.TUNE_LINE2D, line_on)
 
     # plain FP64 scheme: one handle per run, same number of steps
     singles = []
@@ -361,8 +376,8 @@ def run_batched_drops(args):
     s64 = time.perf_counter() - t0
     # accuracy of the FP32 batch against the FP64 runs (same initial state and steps)
     errs_phi, errs_u = [], []
-    for i in range(0, len(runs), max(1, len(runs) // 16)):
-        g32 = batch.fields(run=i)
+    for j, i in enumerate(range(0, len(runs), max(1, len(runs) // 16))):
+        g32 = keep[j]
         g64 = singles[i].fields()
         errs_phi.append(float(np.linalg.norm(g32[4] - g64[4]) / np.linalg.norm(g64[4])))
         den = max(np.linalg.norm(g64[1]), runs[i].sigma / runs[i].nu * math.sqrt(g64[1].size))
@@ -394,7 +409,10 @@ def run_batched_drops(args):
         "config": {"workload": f"batched two-phase drops: {len(runs)} 2D runs, grids 64^2-512^2, "
                                "seeded, FP32, one persistent launch per step",
                    "nodes": nodes, "tuned_ms_per_step": tuned_ms,
-                   "blocks": batch.get_tuning(acm.TUNE_BLOCKS)},
+                   "blocks": batch.get_tuning(acm.TUNE_BLOCKS),
+                   "kernel": "line-marching" if line_on else "tile"},
+        "other_kernel": {"kernel": "tile" if line_on else "line-marching",
+                         "GLUPS": nodes * args.steps / (ms_other / 1e3) / 1e9},
         "roofline": {"bound": "hbm", "achieved": bytes_per_lu * nodes / per_launch / 1e9,
                      "peak": peak, "unit": "GB/s",
                      "frac": bytes_per_lu * nodes / per_launch / 1e9 / peak,

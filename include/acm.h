@@ -286,10 +286,11 @@ enum {
     ACM_TUNE_T3Y = 2,         /* 3D: tile height in y, 8 or 16 */
     ACM_TUNE_GRAPH_STEPS = 3, /* steps per captured CUDA graph, even, >= 2; 0 disables graphs */
     ACM_TUNE_BLOCKS = 4,      /* 2D: persistent CTAs per launch (0 = fill the GPU) */
-    ACM_TUNE_LINE2D = 5       /* 2D single-phase runs periodic on all faces with a width
-                                 that is a multiple of 64: 1 steps them with the
-                                 line-marching kernel (the default for FP32_DEV storage),
-                                 0 with the tile kernel (the default for FP64) */
+    ACM_TUNE_LINE2D = 5       /* 2D runs periodic on all faces (single-phase: width a
+                                 multiple of 64; two-phase: nx >= 64, ny >= 16): 1 steps
+                                 them with the line-marching kernels (the default for
+                                 FP32_DEV storage), 0 with the tile kernel (the default
+                                 for FP64) */
 };
 acm_status acm_set_tuning(acm_handle *h, int key, int value);
 

@@ -411,6 +411,31 @@ acm_status create_common(const acm_params *params, int nruns, acm_handle **out,
     // the line-marching kernel covers single-phase 2D runs that are periodic
     // on all four faces, with a width that is a multiple of its strip
     std::vector<int4> line;
+    if (h->dim == 2 && h->two_phase) {
+        // two-phase line-marching kernel: periodic runs, strips of
+        // line2d_tp_stride() written columns starting at x0 = k stride - 4
+        bool ok = true;
+        for (const RunDesc &d : h->runs) {
+            for (int f = 0; f < 4; ++f) ok &= d.bc[f] == ACM_BC_PERIODIC;
+            ok &= d.nx >= 64 && d.ny >= 16;
+            h->line_gen |= d.rho0 != 1.0 || d.g[0] != 0.0 || d.g[1] != 0.0;
+        }
+        const int sw = line2d_tp_stride();
+        int rows = line2d_tp_rows();
+        auto count = [&](int rr) {
+            long long n = 0;
+            for (const RunDesc &d : h->runs)
+                n += (long long)((d.nx + sw - 1) / sw) * ((d.ny + rr - 1) / rr);
+            return n;
+        };
+        while (ok && rows > 16 && count(rows) < 32LL * h->sms) rows /= 2;
+        for (int r = 0; ok && r < nruns; ++r) {
+            const RunDesc &d = h->runs[r];
+            for (int y0 = 0; y0 < d.ny; y0 += rows)
+                for (int x0 = 0; x0 < d.nx; x0 += sw)
+                    line.push_back(make_int4(r, x0 - 4, y0, std::min(rows, d.ny - y0)));
+        }
+    }
     if (h->dim == 2 && !h->two_phase) {
         bool ok = true;
         for (const RunDesc &d : h->runs) {
@@ -513,9 +538,13 @@ acm_status create_common(const acm_params *params, int nruns, acm_handle **out,
     if (h->dim == 2) {
         if (h->prec == ACM_FP64) step2d_max_blocks_per_sm<double>(h->two_phase);
         else step2d_max_blocks_per_sm<float>(h->two_phase);
-        if (h->nline > 0) {
+        if (h->nline > 0 && !h->two_phase) {
             if (h->prec == ACM_FP64) line2d_prepare<double>();
             else line2d_prepare<float>();
+        }
+        if (h->nline > 0 && h->two_phase) {
+            if (h->prec == ACM_FP64) line2d_tp_prepare<double>();
+            else line2d_tp_prepare<float>();
         }
         if (h->scheme == ACM_SCHEME_MAMES) {
             if (h->prec == ACM_FP64) mames2d_max_blocks_per_sm<double>();
@@ -581,8 +610,10 @@ cudaError_t one_step(acm_handle *h, int from)
                                  h->stream);
     }
     if (h->nline > 0 && h->tune.line2d)
-        return launch_line2d<T>(h->druns, h->dline, h->nline, h->line_gen, in, out, h->derr,
-                                h->stream);
+        return h->two_phase ? launch_line2d_tp<T>(h->druns, h->dline, h->nline, h->line_gen, in,
+                                                  out, h->derr, h->stream)
+                            : launch_line2d<T>(h->druns, h->dline, h->nline, h->line_gen, in,
+                                               out, h->derr, h->stream);
     if (blocks <= 0) blocks = h->sms * step2d_max_blocks_per_sm<T>(h->two_phase);
     return launch_step2d<T>(h->druns, h->dwork, h->nwork, h->two_phase, in, out, h->derr, blocks,
                             h->stream);

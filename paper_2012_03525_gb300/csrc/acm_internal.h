@@ -106,6 +106,17 @@ int line2d_rows();
 int line2d_width();
 template <typename T>
 void line2d_prepare();  // launch attributes (before any capture)
+// 2D two-phase runs periodic on all faces (nx >= 64, ny >= 16): one warp per
+// (run, x0, y0, rows) item; a strip holds 64 columns from x0 (which may be
+// -4) and writes the line2d_tp_stride() columns x0+4 .. of at most
+// line2d_tp_rows() rows.
+int line2d_tp_rows();
+int line2d_tp_stride();
+template <typename T>
+void line2d_tp_prepare();
+template <typename T>
+cudaError_t launch_line2d_tp(const RunDesc *druns, const int4 *dwork, int nwork, bool gen,
+                             Fields<T> in, Fields<T> out, unsigned *derr, cudaStream_t s);
 template <typename T>
 cudaError_t launch_line2d(const RunDesc *druns, const int4 *dwork, int nwork, bool gen,
                           Fields<T> in, Fields<T> out, unsigned *derr, cudaStream_t s);

@@ -33,9 +33,12 @@
 #include <type_traits>
 
 #include "acm_internal.h"
+#include "acm_pair.h"
 
 namespace acm {
 namespace {
+
+using namespace pair;
 
 constexpr int LW = 64;      // columns per strip
 constexpr int LROWS = 32;   // rows per work item (at most)
@@ -53,7 +56,6 @@ constexpr int LAHEAD = LRING - 3; // step y issues row y + LAHEAD (3 rows beyond
 #define ACM_LINE2D_MINB 2
 #endif
 constexpr int LMINB = ACM_LINE2D_MINB;  // FP32: CTAs per SM to aim for (register budget)
-constexpr unsigned FULL = 0xffffffffu;
 
 // shared memory of one warp: LRING rows x 3 fields x 32 lanes own pairs, then
 // LRING rows x 3 fields x 2 edge pairs
@@ -62,73 +64,7 @@ constexpr int RING_ELEMS = LRING * 3 * 32 * 2 + LRING * 3 * 2 * 2;
 template <typename T>
 __device__ __forceinline__ void cp_async_pair(T *dst, const T *src)
 {
-    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(src),
-                 "n"(2 * sizeof(T))
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit()
-{
-    asm volatile("cp.async.commit_group;" ::: "memory");
-}
-template <int N>
-__device__ __forceinline__ void cp_async_wait()
-{
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
-template <typename T>
-struct P2T;
-template <>
-struct P2T<float> {
-    using type = float2;
-};
-template <>
-struct P2T<double> {
-    using type = double2;
-};
-template <typename T>
-using P2 = typename P2T<T>::type;
-
-__device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
-__device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
-// every operation an explicit round-to-nearest intrinsic (never contracted)
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ double2 add2(double2 a, double2 b)
-{
-    return make_double2(__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y));
-}
-__device__ __forceinline__ double2 mul2(double2 a, double2 b)
-{
-    return make_double2(__dmul_rn(a.x, b.x), __dmul_rn(a.y, b.y));
-}
-__device__ __forceinline__ double2 fma2(double2 a, double2 b, double2 c)
-{
-    return make_double2(__fma_rn(a.x, b.x, c.x), __fma_rn(a.y, b.y, c.y));
-}
-__device__ __forceinline__ float add1(float a, float b) { return __fadd_rn(a, b); }
-__device__ __forceinline__ float mul1(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ float fma1(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-__device__ __forceinline__ double add1(double a, double b) { return __dadd_rn(a, b); }
-__device__ __forceinline__ double mul1(double a, double b) { return __dmul_rn(a, b); }
-__device__ __forceinline__ double fma1(double a, double b, double c) { return __fma_rn(a, b, c); }
-
-// 1 / rho^{n+1}.  FP32: the hardware approximation (1 ulp) suffices, since
-// it only scales the increment of u, which is O(Ma^2) relative to u.
-__device__ __forceinline__ float recip(float x)
-{
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ double recip(double x) { return __drcp_rn(x); }
-
-template <typename T>
-__device__ __forceinline__ P2<T> splat(T a)
-{
-    return mk(a, a);
+    cp_async<2 * sizeof(T)>(dst, src);
 }
 
 // coefficient pairs of one run (negated copies where a term is subtracted)

@@ -13,7 +13,7 @@ import pytest
 
 from paper_2012_03525_gb300 import acm, build
 from paper_2012_03525_gb300 import workloads as wl
-from test_parity_gpu import assert_parity, run_both, _smooth
+from test_parity_gpu import assert_parity, rel_l2, run_both, _flow, _smooth
 
 pytestmark = pytest.mark.gpu
 
@@ -133,3 +133,91 @@ def test_line2d_tgv64_fp64_1000_steps(oracle_lib):
     ref, got = run_both(oracle_lib, (n, n), state, steps, gpu_kw=LINE, nu=nu)
     assert_parity(ref, got)
     assert abs(got[0].sum() - state[0].sum()) < 1e-12 * state[0].sum()
+
+
+# ------------------------------------------------------------ two-phase form
+def _drop_state(shape, seed, R=None, flow=True):
+    ny, nx = shape
+    R = 0.3 * min(shape) if R is None else R
+    X, Y = np.meshgrid(np.arange(nx) - (nx - 1) / 2 + 0.3, np.arange(ny) - (ny - 1) / 2 - 0.2)
+    phi = -np.tanh(2 * (np.hypot(X, Y * 1.1) - R) / 4.0)
+    rng = np.random.default_rng(seed)
+    u = _flow(rng, shape) if flow else np.zeros(shape)
+    v = _flow(rng, shape) if flow else np.zeros(shape)
+    return [np.ones(shape), u, v, phi]
+
+
+TP = dict(nu=0.1, two_phase=True, sigma=1e-2, W=4.0, M=0.3)
+
+
+@pytest.mark.parametrize("shape", [(64, 64), (16, 130), (33, 71), (100, 112), (70, 57 + 64)])
+def test_line2d_tp_periodic_fp64(oracle_lib, shape):
+    """Strips of 56 written columns over 64 held ones: one wrapping strip,
+    odd widths and heights, the shortest allowed height (16), a last strip
+    of a few columns."""
+    st = _drop_state(shape, sum(shape))
+    ref, got = run_both(oracle_lib, shape, st, 60, gpu_kw=LINE, **TP)
+    assert_parity(ref, got)
+
+
+def test_line2d_tp_general_instantiation_fp64(oracle_lib):
+    """Gravity with the Boussinesq drop force (r_rho = 1.15) selects the
+    general instantiation."""
+    shape = (72, 96)
+    st = _drop_state(shape, 5)
+    ref, got = run_both(oracle_lib, shape, st, 60, gpu_kw=LINE, g=(0.0, -1e-5, 0.0),
+                        rho_ratio=1.15, **TP)
+    assert_parity(ref, got)
+
+
+def test_line2d_tp_fp32(oracle_lib):
+    shape = (96, 128)
+    st = _drop_state(shape, 6)
+    ref, got = run_both(oracle_lib, shape, st, 200, gpu_kw={"precision": acm.FP32_DEV}, **TP)
+    assert rel_l2(got[4], ref[4]) < 1e-6
+    for k in (1, 2):
+        assert rel_l2(got[k], ref[k]) < 1e-4
+    assert rel_l2(got[0] - 1, ref[0] - 1) < 1e-3
+
+
+def test_line2d_tp_batched_drops_match_oracle(oracle_lib):
+    """Runs of the seeded drop batch (uneven grids, different sigma) in one
+    handle on the two-phase line kernel: every run equals its oracle run."""
+    co = oracle_lib
+    spec = wl.batch_drops()
+    idx = [i for i in range(len(spec)) if spec[i].n <= 150][:5]
+    params, states = [], []
+    for i in idx:
+        d = spec[i]
+        params.append(acm.make_params((d.n, d.n), nu=d.nu, two_phase=True, sigma=d.sigma,
+                                      W=d.W, M=d.M))
+        rho, u, v, phi = wl.drop2d(d.n, d.radius, d.W, eps=d.eps)
+        rng = np.random.default_rng(i)
+        states.append([rho, _flow(rng, rho.shape), _flow(rng, rho.shape), phi])
+    with acm.Solver(params) as s:
+        s.set_tuning(acm.TUNE_LINE2D, 1)
+        for r, st in enumerate(states):
+            s.set_fields(st[0], st[1], st[2], None, st[3], run=r)
+        s.step(40)
+        for r, i in enumerate(idx):
+            d = spec[i]
+            got = list(s.fields(run=r))
+            rho, u, v, phi = [x.copy() for x in states[r]]
+            co.step(co.make_params((d.n, d.n), nu=d.nu, two_phase=True, sigma=d.sigma, W=d.W,
+                                   M=d.M), rho, u, v, None, phi, nsteps=40)
+            assert_parity([rho, u, v, None, phi], got)
+
+
+def test_line2d_tp_matches_tile_kernel_fp32():
+    shape = (128, 192)
+    st = _drop_state(shape, 8)
+    out = []
+    for line in (1, 0):
+        with acm.Solver(acm.make_params(shape, precision=acm.FP32_DEV, **TP)) as s:
+            s.set_tuning(acm.TUNE_LINE2D, line)
+            s.set_fields(st[0], st[1], st[2], None, st[3])
+            s.step(100)
+            out.append(s.fields())
+    assert rel_l2(out[0][4], out[1][4]) < 1e-6
+    for k in (1, 2):
+        assert rel_l2(out[0][k], out[1][k]) < 1e-4
