@@ -347,7 +347,7 @@ typedef struct acm_closure acm_closure;
 
 /* number of weights and biases (11011) */
 size_t acm_closure_num_params(void);
-/* grid nx x ny (nx a multiple of 16, ny of 8), BATCH states per call */
+/* grid nx x ny (both multiples of 16), BATCH states per call */
 acm_status acm_closure_create(int nx, int ny, int batch, acm_closure **out);
 acm_status acm_closure_set_stream(acm_closure *c, void *stream);
 /* normalisation scales s_rho, s_u, s_u (s_u shared by u and v) */

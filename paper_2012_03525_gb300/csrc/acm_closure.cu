@@ -29,7 +29,6 @@ namespace {
 
 typedef __nv_bfloat16 bf16;
 
-constexpr int CTH = 8, CTW = 16;  // pixel tile (128 pixels: the M of the MMAs)
 
 // real / padded channel counts of the three layers
 constexpr int NL = 3;
@@ -42,23 +41,27 @@ enum { OUT_RELU_BF16 = 0, OUT_MASK_BF16 = 1, OUT_F32_NCHW = 2 };
 // One 3x3 convolution layer (or its data gradient) as per-tap GEMMs issued by
 // one thread of the CTA: for each tap (dy, dx) and 16-channel slice,
 //   D[p, co] += sum_ci X[p + (dy, dx), ci] A[co, (tap, ci)]
-// with M = the 128 pixels of an 8 x 16 tile, N = CO, K = 16, BF16 operands
+// with M = the 128 pixels of a 16 x 8 tile, N = CO, K = 16, BF16 operands
 // from shared memory and the FP32 accumulator D in tensor memory (TMEM).
 // Both operands are in the no-swizzle K-major layout of 8 x 16-byte "core
-// matrices": X is staged as three copies shifted by dx (each 10 rows x 16
-// columns, periodic wrap applied while staging), so the 128 rows of the A
-// operand of tap (dy, dx) are the contiguous pixels (dy + 1) * 16 .. of copy
-// dx; the weights as [tap][ci / 8][co][8].  Persistent CTAs of 4 warps walk
+// matrices": the (16 + 2) x (8 + 2) halo of X is staged once (periodic wrap
+// applied while staging); the 8-pixel row groups of the A operand of tap
+// (dy, dx) are the tile rows, which start at halo pixel (row + dy + 1) * 10
+// + dx + 1, so one descriptor with a 10-pixel stride between groups covers
+// the tap; the weights as [tap][ci / 8][co][8].  Persistent CTAs of 4 warps walk
 // the tiles, staging the next tile (cp.async) while the tensor cores work on
 // the current one; the epilogue reads D with tcgen05.ld (warp w holds TMEM
-// lanes 32w .. 32w + 31, i.e. tile rows 2w and 2w + 1).
+// lanes 32w .. 32w + 31, i.e. tile rows 4w .. 4w + 3).
 constexpr int TC_THREADS = 128;
-constexpr int TC_HP = (CTH + 2) * CTW;  // pixels of one dx-shifted halo copy
+// pixel tile of every convolution kernel: 16 rows x 8 columns (M = 128
+// pixels, eight per row, so the 8-pixel core-matrix groups of a tap's
+// operand are the tile rows, equally spaced in one staged halo)
+constexpr int FTH = 16, FTW = 8;
+constexpr int FHW = FTW + 2, FHP = (FTH + 2) * FHW;  // halo row width, halo pixels
 
 template <int CI, int CO>
 struct TcGeo {
-    static constexpr int XCOPY = TC_HP * CI * 2;  // bytes of one dx copy
-    static constexpr int XBUF = 3 * XCOPY;        // one staged tile
+    static constexpr int XBUF = FHP * CI * 2;     // one staged forward tile
     static constexpr int WBYTES = 9 * CI * CO * 2;
     static constexpr int BAR = 2 * XBUF + WBYTES;
     static constexpr int SMEM = BAR + 16;
@@ -150,27 +153,20 @@ constexpr int TC_WAIT_LIMIT = 1 << 22;
 // index in [-1, n] wrapped into [0, n)
 __device__ __forceinline__ int wrap1(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
-// Three dx-shifted copies of the (8 + 2) x 16 halo of the 8 x 16 tile at
-// (y0, x0) of image xi (NHWC, periodic): chunk j (channels 8j .. 8j + 7) of
-// halo pixel (hr, c) of copy dx at [dx][j][hr * 16 + c][8].  Each thread owns
-// one (c, j) pair (consecutive threads: consecutive 16-byte chunks in global
-// memory) and every NSUB-th halo row of each copy.
+// The (16 + 2) x (8 + 2) halo of the 16 x 8 tile at (y0, x0) of image xi
+// (NHWC, periodic): chunk j (channels 8j .. 8j + 7) of halo pixel hp = hr * 10
+// + c at [j][hp][8].  Consecutive threads take consecutive 16-byte chunks of
+// global memory (the chunks of a pixel, then the next pixel of the row).
 template <int CI>
-__device__ __forceinline__ void stage_halo(unsigned char *dst, const bf16 *xi, int H, int W,
+__device__ __forceinline__ void stage_tile(unsigned char *dst, const bf16 *xi, int H, int W,
                                            int y0, int x0, int tid)
 {
-    constexpr int NJ = CI / 8, NCJ = CTW * NJ, NSUB = TC_THREADS / NCJ;
-    constexpr int XCOPY = TC_HP * CI * 2;
-    const int cj = tid % NCJ, sub = tid / NCJ;
-    const int j = cj % NJ, c = cj / NJ;
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        const int gx = wrap1(x0 + c + d - 1, W);
-        for (int hr = sub; hr < CTH + 2; hr += NSUB) {
-            const int gy = wrap1(y0 - 1 + hr, H);
-            cp_async16(dst + d * XCOPY + (j * TC_HP + hr * CTW + c) * 16,
-                       xi + ((size_t)gy * W + gx) * CI + 8 * j);
-        }
+    constexpr int NJ = CI / 8;
+    for (int i = tid; i < FHP * NJ; i += TC_THREADS) {
+        const int hp = i / NJ, j = i - hp * NJ;
+        const int hr = hp / FHW, c = hp - hr * FHW;
+        const int gy = wrap1(y0 - 1 + hr, H), gx = wrap1(x0 - 1 + c, W);
+        cp_async16(dst + (j * FHP + hp) * 16, xi + ((size_t)gy * W + gx) * CI + 8 * j);
     }
 }
 
@@ -186,7 +182,7 @@ __global__ void __launch_bounds__(TC_THREADS)
     uint64_t *bar = reinterpret_cast<uint64_t *>(tsm + G::BAR);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(tsm + G::BAR + 8);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int tiles_x = W / CTW, tiles_img = tiles_x * (H / CTH);
+    const int tiles_x = W / FTW, tiles_img = tiles_x * (H / FTH);
 
     // weights [co][tap * CI + ci] -> [tap][ci / 8][co][8] (16-byte chunks)
     for (int i = tid; i < CO * 9 * CI / 8; i += TC_THREADS) {
@@ -207,12 +203,11 @@ __global__ void __launch_bounds__(TC_THREADS)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
 
-    // stage tile t (periodic halo, three dx-shifted copies) into buffer b:
-    // chunk j of pixel (hr, c) of copy dx at [dx][j][hr * 16 + c][8]
+    // stage tile t (periodic halo) into buffer b
     auto stage = [&](int t, int b) {
         const int img = t / tiles_img, r = t - img * tiles_img;
-        const int y0 = (r / tiles_x) * CTH, x0 = (r % tiles_x) * CTW;
-        stage_halo<CI>(tsm + b * G::XBUF, x + (size_t)img * H * W * CI, H, W, y0, x0, tid);
+        const int y0 = (r / tiles_x) * FTH, x0 = (r % tiles_x) * FTW;
+        stage_tile<CI>(tsm + b * G::XBUF, x + (size_t)img * H * W * CI, H, W, y0, x0, tid);
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
 
@@ -242,9 +237,11 @@ __global__ void __launch_bounds__(TC_THREADS)
                 const int dy = tap / 3, dxi = tap % 3;  // dy + 1, dx + 1
 #pragma unroll
                 for (int kc = 0; kc < CI / 16; ++kc, ++k) {
-                    const uint64_t ad = tc_desc(xb + dxi * G::XCOPY + 2 * kc * TC_HP * 16 +
-                                                    dy * CTW * 16,
-                                                TC_HP * 16, 128);
+                    // A: 8-pixel group g (tile row g) of tap (dy, dx) starts at
+                    // halo pixel (g + dy) * 10 + dx: stride 10 pixels between
+                    // groups, FHP pixels between the two 8-channel chunks of K
+                    const uint64_t ad = tc_desc(xb + 2 * kc * FHP * 16 + (dy * FHW + dxi) * 16,
+                                                FHP * 16, FHW * 16);
                     const uint64_t bd = tc_desc(wb + (tap * (CI / 8) + 2 * kc) * CO * 16, CO * 16,
                                                 128);
                     tc_mma(tmem, ad, bd, idesc, k > 0);
@@ -270,10 +267,11 @@ __global__ void __launch_bounds__(TC_THREADS)
         tc_load_row<CO>(tmem + ((uint32_t)(32 * warp) << 16), v);
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 
-        // epilogue: this thread's pixel p = 32 warp + lane of the tile
+        // epilogue: this thread's pixel p = 32 warp + lane of the tile (row
+        // p / 8, column p % 8)
         const int img = t / tiles_img, r = t - img * tiles_img;
         const int p = 32 * warp + lane;
-        const int py = (r / tiles_x) * CTH + p / CTW, px = (r % tiles_x) * CTW + p % CTW;
+        const int py = (r / tiles_x) * FTH + p / FTW, px = (r % tiles_x) * FTW + p % FTW;
         const size_t pix = (size_t)img * H * W + (size_t)py * W + px;
         if (MODE == OUT_F32_NCHW) {
             float *o = static_cast<float *>(out);
@@ -334,7 +332,7 @@ cudaError_t conv_tc(const bf16 *x, const bf16 *A, const float *bias, const bf16 
         const int per = std::max(1, std::min(8, smem / (G::SMEM + 1024)));
         grid_cap = std::max(1, sms) * per;
     }
-    const int ntiles = batch * (H / CTH) * (W / CTW);
+    const int ntiles = batch * (H / FTH) * (W / FTW);
     const int grid = std::min(ntiles, grid_cap);
     k_conv_tc<CI, CO, MODE><<<grid, TC_THREADS, G::SMEM, s>>>(x, A, bias, mask, out, H, W, nout,
                                                               ntiles, err);
@@ -347,18 +345,18 @@ cudaError_t conv_tc(const bf16 *x, const bf16 *A, const float *bias, const bf16 
 // CTA walks (columns tap * CI .. tap * CI + CI - 1).  Both operands are read
 // MN-major (the channel index contiguous in 16-byte core-matrix rows, one row
 // per pixel), i.e. in the re-blocked NHWC layout the forward kernel stages:
-// dY as [co / 8][pixel][8], X as the three dx-shifted halo copies
-// [dx][ci / 8][halo pixel][8], so tap (dy, dx) is copy dx started (dy + 1) * 16
-// pixels in.  M = 128 is the smallest MMA height; rows co >= CO read other
+// the 16 x 8 tile's dY as [co / 8][pixel][8] and its X halo as [ci / 8][halo
+// pixel][8], so the 16 pixels (two tile rows) of K step k of tap (dy, dx)
+// are two 8-pixel groups of the halo, 10 pixels apart, the first at halo
+// pixel (2k + dy + 1) * 10 + dx + 1.  M = 128 is the smallest MMA height; rows co >= CO read other
 // shared memory and land in accumulator rows no one reads.  One CTA per SM
 // (9 * CI columns of TMEM), persistent over the tiles of all images; the
 // bias gradient sum_p dY[p, co] is summed by threads from the staged tile.
 template <int CI, int CO>
 struct WgGeo {
-    static constexpr int TP = CTH * CTW;                   // 128 pixels per tile
+    static constexpr int TP = FTH * FTW;                   // 128 pixels per tile
     static constexpr int YBUF = 16 * TP * 16;              // dY staging, room for 16 row groups
-    static constexpr int XCOPY = TC_HP * CI * 2;           // one dx copy of the X halo tile
-    static constexpr int BUF = YBUF + 3 * XCOPY;           // one staged tile
+    static constexpr int BUF = YBUF + FHP * CI * 2;        // one staged tile (dY, X halo)
     static constexpr int BAR = 2 * BUF;
     static constexpr int SMEM = BAR + 16;
     static constexpr int NCOL = 9 * CI;
@@ -377,7 +375,7 @@ __global__ void __launch_bounds__(TC_THREADS)
     uint64_t *bar = reinterpret_cast<uint64_t *>(wsm + G::BAR);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(wsm + G::BAR + 8);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int tiles_x = W / CTW, tiles_img = tiles_x * (H / CTH);
+    const int tiles_x = W / FTW, tiles_img = tiles_x * (H / FTH);
 
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(bar)) : "memory");
@@ -390,23 +388,24 @@ __global__ void __launch_bounds__(TC_THREADS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    // stage tile t into buffer b: dY re-blocked [co/8][p][8]; X as three
-    // dx-shifted halo copies [dx][ci/8][hp][8] (periodic wrap while staging)
-    // dY chunks: each thread owns one (column c, channel chunk j) pair of
-    // the tile and every YSUB-th row (consecutive threads: consecutive
-    // 16-byte chunks in global memory)
-    constexpr int YNJ = CO / 8, YNCJ = CTW * YNJ, YSUB = TC_THREADS / YNCJ;
-    const int ycj = tid % YNCJ, ysub = tid / YNCJ;
-    const int yj = ycj % YNJ, yc = ycj / YNJ;
+    // stage tile t into buffer b: dY re-blocked [co/8][p][8] (p = 8 row +
+    // column); X halo [ci/8][hp][8] (periodic wrap while staging).  dY chunk
+    // i = p * YNJ + j: consecutive threads take consecutive 16-byte chunks of
+    // global memory, and every thread keeps the same channel chunk j
+    constexpr int YNJ = CO / 8;
+    static_assert(TC_THREADS % YNJ == 0, "a thread's dY chunks share one channel chunk");
+    const int yj = tid % YNJ;
     auto stage = [&](int t, int b) {
         const int img = t / tiles_img, r = t - img * tiles_img;
-        const int y0 = (r / tiles_x) * CTH, x0 = (r % tiles_x) * CTW;
+        const int y0 = (r / tiles_x) * FTH, x0 = (r % tiles_x) * FTW;
         unsigned char *buf = wsm + b * G::BUF;
         const bf16 *dyi = dy + (size_t)img * H * W * CO;
-        for (int row = ysub; row < CTH; row += YSUB)
-            cp_async16(buf + (yj * G::TP + row * CTW + yc) * 16,
-                       dyi + ((size_t)(y0 + row) * W + x0 + yc) * CO + 8 * yj);
-        stage_halo<CI>(buf + G::YBUF, x + (size_t)img * H * W * CI, H, W, y0, x0, tid);
+        for (int i = tid; i < G::TP * YNJ; i += TC_THREADS) {
+            const int p = i / YNJ;
+            cp_async16(buf + (yj * G::TP + p) * 16,
+                       dyi + ((size_t)(y0 + p / FTW) * W + x0 + p % FTW) * CO + 8 * yj);
+        }
+        stage_tile<CI>(buf + G::YBUF, x + (size_t)img * H * W * CI, H, W, y0, x0, tid);
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
 
@@ -441,8 +440,8 @@ __global__ void __launch_bounds__(TC_THREADS)
                     // byte offset that between 8-channel (M/N) groups (as for
                     // K-major operands; checked against the CPU by a probe)
                     const uint64_t ad = tc_desc(yb + k * 256, 128, G::TP * 16);
-                    const uint64_t bd =
-                        tc_desc(xb + dxi * G::XCOPY + dy * CTW * 16 + k * 256, 128, TC_HP * 16);
+                    const uint64_t bd = tc_desc(xb + ((2 * k + dy) * FHW + dxi) * 16, FHW * 16,
+                                                FHP * 16);
                     tc_mma(tmem + tap * CI, ad, bd, idesc, (first && k == 0) ? 0u : 1u);
                 }
             }
@@ -456,10 +455,10 @@ __global__ void __launch_bounds__(TC_THREADS)
         const int tn = t + gridDim.x;
         if (tn < ntiles) stage(tn, b ^ 1);
         // bias gradient: this thread's own staged dY chunks of the tile
-        for (int row = ysub; row < CTH; row += YSUB) {
+        for (int i = tid; i < G::TP * YNJ; i += TC_THREADS) {
             __align__(16) bf16 h[8];
             *reinterpret_cast<uint4 *>(h) =
-                *reinterpret_cast<const uint4 *>(buf + (yj * G::TP + row * CTW + yc) * 16);
+                *reinterpret_cast<const uint4 *>(buf + (yj * G::TP + i / YNJ) * 16);
 #pragma unroll
             for (int e = 0; e < 8; ++e) bacc[e] += __bfloat162float(h[e]);
         }
@@ -527,7 +526,7 @@ cudaError_t wgrad_tc(const bf16 *dy, const bf16 *x, float *partial, int H, int W
         const int per = std::max(1, std::min(512 / G::TCOLS, smem / (G::SMEM + 1024)));
         grid_cap = std::max(1, sms) * per;
     }
-    const int ntiles = batch * (H / CTH) * (W / CTW);
+    const int ntiles = batch * (H / FTH) * (W / FTW);
     const int grid = std::min(ntiles, grid_cap);
     *nparts = grid;
     k_wgrad_tc<CI, CO><<<grid, TC_THREADS, G::SMEM, s>>>(dy, x, partial, H, W, ntiles, err);
@@ -894,8 +893,8 @@ size_t acm_closure_num_params(void) { return n_params(); }
 acm_status acm_closure_create(int nx, int ny, int batch, acm_closure **out)
 {
     if (out) *out = nullptr;
-    if (!out || nx < CTW || ny < CTH || nx % CTW || ny % CTH || batch < 1)
-        return cfail(nullptr, ACM_EINVAL, "closure grid must be a multiple of 16 x 8, batch >= 1");
+    if (!out || nx < 16 || ny < 16 || nx % 16 || ny % 16 || batch < 1)
+        return cfail(nullptr, ACM_EINVAL, "closure grid must be a multiple of 16 x 16, batch >= 1");
     acm_closure *c = new (std::nothrow) acm_closure();
     if (!c) return cfail(nullptr, ACM_ENOMEM, "host allocation failed");
     c->nx = nx;
@@ -903,7 +902,7 @@ acm_status acm_closure_create(int nx, int ny, int batch, acm_closure **out)
     c->batch = batch;
     c->nparam = n_params();
     const size_t HW = (size_t)nx * ny, NB = HW * batch;
-    const int tiles_img = (nx / CTW) * (ny / CTH);
+    const int tiles_img = (nx / FTW) * (ny / FTH);
     // weight-gradient partials: one per CTA, at most two CTAs per SM
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
