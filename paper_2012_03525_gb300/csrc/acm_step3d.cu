@@ -16,13 +16,15 @@
 //   * Eq. (2.10) is evaluated for plane z+1 on the tile grown by one node:
 //     the own nodes in registers, the one-node ring by 100 threads; Delta rho
 //     of the own nodes stays in a register queue (z-1, z, z+1), the tile plane
-//     goes to shared memory for the x/y neighbours, so
+//     goes to shared memory (one window per plane slot, so its index is a
+//     compile-time constant) for the x/y neighbours, so
 //     d_a rho^{n+1} - d_a rho^n of Eq. (2.11) is a centred difference of
 //     Delta rho.
 //   * Eq. (2.11) for plane z; u^{n+1} = u + (RHS - Delta rho u) / rho^{n+1}.
-//   * Every thread ORs whether its outputs are finite (the sum of a node's
-//     four new values is finite only if each is); one flag per CTA
-//     (ERR_NONFINITE) reports a blow-up without a separate pass.
+//   * Every thread keeps a running sum of its outputs (finite only if every
+//     value added is finite); one flag per CTA (ERR_NONFINITE) reports a
+//     blow-up without a separate pass.  Output addresses advance by one
+//     plane per step.
 // Storage is padded by T3PAD ghost nodes in x and y (not in z).  Every output
 // node on the first/last two columns/rows is also written to its periodic
 // image in the ghost layers, so the next step's TMA boxes never wrap in x/y;
@@ -111,7 +113,7 @@ struct Geo {
     static constexpr int RW1 = T3X + 2, RH1 = TY + 2, P1 = RW1 * RH1;
     static constexpr int NRING = 2 * T3X + 2 * RH1;  // one-node ring around the tile
     static constexpr int PLANE_ELEMS = PLANE_BYTES / (int)sizeof(T);
-    static constexpr int SD_BYTES = ((2 * P1 * (int)sizeof(T) + 127) / 128) * 128;
+    static constexpr int SD_BYTES = ((NSLOT * P1 * (int)sizeof(T) + 127) / 128) * 128;
     static constexpr int BAR_OFFSET = NSLOT * 4 * PLANE_BYTES + SD_BYTES;
     static constexpr int SMEM = BAR_OFFSET + 128;
     static constexpr int NT = T3X * TY / 2;
@@ -354,7 +356,7 @@ __global__ void __launch_bounds__(T3X *TY / 2, Prec<T>::MINB * 16 / TY)
     constexpr int NSLOT = G::NSLOT, RW = G::RW, RW1 = G::RW1, PE = G::PLANE_ELEMS, P1 = G::P1;
     extern __shared__ __align__(128) unsigned char smem[];
     T *S = reinterpret_cast<T *>(smem);        // plane (slot s, field f) at (4 s + f) PE
-    T *SD = S + NSLOT * 4 * PE;                  // two Delta-rho windows of P1
+    T *SD = S + NSLOT * 4 * PE;                  // NSLOT Delta-rho windows of P1 (one per plane slot)
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + G::BAR_OFFSET);
     int *s_abort = reinterpret_cast<int *>(bar + NSLOT);
 
@@ -400,7 +402,7 @@ __global__ void __launch_bounds__(T3X *TY / 2, Prec<T>::MINB * 16 / TY)
         ring_c = (ly + 1) * RW + (lx + 1);
     }
     const long long PX = R.px, PXY = R.px * R.py;
-    bool bad = false;  // a non-finite output of this thread
+    P2 fin = splat(T(0));  // running sum of this thread's outputs (non-finite on a blow-up)
 
     // Every chunk puts plane zbeg-2 in slot 0, so plane p sits in slot
     // (p - zbeg + 2) % NSLOT; the loop below is unrolled by NSLOT so every
@@ -491,8 +493,8 @@ __global__ void __launch_bounds__(T3X *TY / 2, Prec<T>::MINB * 16 / TY)
         load_col(1, Q[1]);
         load_col(2, Q[2]);
         load_col(3, Q[3]);
-        delta_rho(0, 1, 2, SD + ((zbeg - 1) & 1) * P1, Q[0], Q[1], Q[2], D[1]);
-        delta_rho(1, 2, 3, SD + (zbeg & 1) * P1, Q[1], Q[2], Q[3], D[2]);
+        delta_rho(0, 1, 2, SD + 1 * P1, Q[0], Q[1], Q[2], D[1]);
+        delta_rho(1, 2, 3, SD + 2 * P1, Q[1], Q[2], Q[3], D[2]);
         __syncthreads();  // plane zbeg-2 is no longer read
         if (tid == 0 && zbeg + NSLOT - 2 <= zlast) issue(0, zbeg + NSLOT - 2, x0, y0);
 
@@ -505,6 +507,7 @@ __global__ void __launch_bounds__(T3X *TY / 2, Prec<T>::MINB * 16 / TY)
         const bool edge = gx < T3PAD || gx >= nx - T3PAD || gya < T3PAD || gyb >= ny - T3PAD;
         const long long base_a =
             R.off + R.zg * PXY + (long long)(gya + T3PAD) * PX + (gx + T3PAD);
+        long long gcur = base_a + (long long)zbeg * PXY;  // storage index of plane z
         auto store2 = [&](long long ga, T ra, T ua, T va, T wa, T rb, T ub, T vb, T wb) {
             if (plain_tile) {
                 out.f[F_R][ga] = ra;
@@ -539,8 +542,8 @@ __global__ void __launch_bounds__(T3X *TY / 2, Prec<T>::MINB * 16 / TY)
             constexpr int SM = (J + 1) % NSLOT, S0 = (J + 2) % NSLOT;  // planes z-1, z
             constexpr int S1 = (J + 3) % NSLOT, S2 = (J + 4) % NSLOT;  // planes z+1, z+2
             const int z = zg + J;
-            // One barrier per plane: after it, plane z-1 (slot SM) and the
-            // Delta-rho window of z-1 are free, the window of z written in
+            // One barrier per plane: after it, plane z-1 (slot SM) is free,
+            // the Delta-rho window of z (slot S0) written in
             // the previous step is complete, and every wait of the previous
             // step has returned, so the abort flag reads the same in every
             // thread.  Plane z and z+1 were waited for by each thread itself.
@@ -550,10 +553,10 @@ __global__ void __launch_bounds__(T3X *TY / 2, Prec<T>::MINB * 16 / TY)
             wait(S2);
             load_col(S2, Q[S2]);
             // harmless on stale data if the wait gave up (checked at the next barrier)
-            delta_rho(S0, S1, S2, SD + ((z + 1) & 1) * P1, Q[S0], Q[S1], Q[S2], D[S1]);
+            delta_rho(S0, S1, S2, SD + S1 * P1, Q[S0], Q[S1], Q[S2], D[S1]);
 
             const T *pr = S + S0 * 4 * PE, *pu = pr + PE, *pv = pr + 2 * PE, *pw = pr + 3 * PE;
-            const T *dz = SD + (z & 1) * P1;
+            const T *dz = SD + S0 * P1;
             const Col<T> &Xm = Q[SM], &X0 = Q[S0], &Xp = Q[S1];
             const P2 r[7] = {mk(X0.r[0], X0.r[1]), mk(pr[ca + 1], pr[cb + 1]),
                              mk(pr[ca - 1], pr[cb - 1]), mk(X0.r[1], pr[cb + RW]),
@@ -577,11 +580,12 @@ __global__ void __launch_bounds__(T3X *TY / 2, Prec<T>::MINB * 16 / TY)
                              mk(D[SM][0], D[SM][1])};
             P2 rn, un, vn, wn;
             node_update2<T, GEN>(r, u, v, w, d, K, rn, un, vn, wn);
-            {   // blow-up check on the nodes inside the grid
+            {   // blow-up check on the nodes inside the grid: a running sum
                 const P2 c2 = add2(add2(rn, un), add2(vn, wn));
-                bad |= !isfinite(add1(own_a ? c2.x : T(0), own_b ? c2.y : T(0)));
+                fin = add2(fin, plain_tile ? c2 : mk(own_a ? c2.x : T(0), own_b ? c2.y : T(0)));
             }
-            store2(base_a + (long long)z * PXY, rn.x, un.x, vn.x, wn.x, rn.y, un.y, vn.y, wn.y);
+            store2(gcur, rn.x, un.x, vn.x, wn.x, rn.y, un.y, vn.y, wn.y);
+            gcur += PXY;
             return true;
         };
 
@@ -590,6 +594,7 @@ __global__ void __launch_bounds__(T3X *TY / 2, Prec<T>::MINB * 16 / TY)
         __syncthreads();  // every read of this chunk's planes is done
         if (*s_abort) break;
     }
+    const bool bad = !isfinite(add1(fin.x, fin.y));
     if (__syncthreads_or(bad) && tid == 0) atomicOr(err, ERR_NONFINITE);
 }
 
