@@ -82,7 +82,10 @@ enum { K_MIRROR = 0, K_WET = 1 };
 #ifndef ACM_TP3D_ZCH
 #define ACM_TP3D_ZCH 8
 #endif
-constexpr int BX = 32, BY = 8, ZCH = ACM_TP3D_ZCH;
+#ifndef ACM_TP3D_BY
+#define ACM_TP3D_BY 8
+#endif
+constexpr int BX = 32, BY = ACM_TP3D_BY, ZCH = ACM_TP3D_ZCH;
 constexpr int WX = BX + 2, WY = BY + 2, WP = WX * WY;
 
 // index c in [-1, n + BX] wrapped into [0, n) (a full modulo only for grids
