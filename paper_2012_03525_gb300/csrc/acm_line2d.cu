@@ -18,8 +18,9 @@
 //     one commit group, and a lane waits for the group of the row it needs
 //     next while the next LAHEAD - 2 rows are still in flight, so memory
 //     latency overlaps several rows of arithmetic.
-//   * y-neighbours stay in registers: rows y-1 .. y+2 of the pair (and of the
-//     edge pairs) form a queue, advanced one row per step.
+//   * y-neighbours stay in registers: rows y-1 .. y+2 of the pair form a
+//     queue, advanced one row per step; the edge lanes read their outside
+//     pairs from the ring where they are used.
 //   * Eq. (2.10) is evaluated one row ahead (row y+1) for the own pair and,
 //     in the two edge lanes, for the node just outside the strip, so that
 //     d_a rho^{n+1} - d_a rho^n of Eq. (2.11) is a centred difference of
