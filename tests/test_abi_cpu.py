@@ -160,3 +160,16 @@ def test_stability_ratio_von_neumann(lib):
     p = acm.make_params((1, 2), nu=0.0)
     assert acm.stability_ratio(p, np.array([0.0, 1e-3]), np.zeros(2)) == math.inf
     assert acm.stability_ratio(p, np.zeros(2), np.zeros(2)) == 0.0
+
+
+@pytest.mark.parametrize("nx,ny,batch", [(8, 16, 1), (16, 8, 1), (24, 16, 1), (32, 40, 1),
+                                         (32, 32, 0), (0, 0, 1)])
+def test_closure_grid_rejected_before_any_gpu_work(lib, nx, ny, batch):
+    """The closure's convolution tiles are 16 x 8 pixels and its staging
+    needs both grid sides a multiple of 16: other grids (or an empty batch)
+    are refused by acm_closure_create with ACM_EINVAL and a message."""
+    c = ctypes.c_void_p()
+    st = lib.acm_closure_create(nx, ny, batch, ctypes.byref(c))
+    assert st == acm.EINVAL
+    assert not c.value
+    assert "multiple of 16" in lib.acm_closure_last_error(None).decode()
