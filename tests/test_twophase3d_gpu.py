@@ -44,6 +44,8 @@ def _state(shape, phi, amp=2e-3, walls=False):
     ((20, 24, 28), [0] * 6, 90.0),
     ((17, 22, 33), [0, 0, 0, 0, 1, 1], 60.0),
     ((16, 20, 24), [0, 0, 0, 0, 1, 1], 150.0),
+    ((13, 21, 19), [0] * 6, 90.0),                 # odd ny: pairs whose second node is outside
+    ((11, 37, 35), [0, 0, 0, 0, 1, 1], 120.0),     # three tile rows, the last one short and odd
 ])
 def test_two_phase_3d_fp64(oracle_lib, shape, bc, theta):
     walls = bc[4] == 1
@@ -216,12 +218,13 @@ def _quarter_state(shape, walls=True, amp=2e-3):
     return [np.ones(shape), u, v, w, phi]
 
 
-@pytest.mark.parametrize("theta", [90.0, 150.0])
-def test_two_phase_3d_symmetry_planes_fp64(oracle_lib, theta):
+@pytest.mark.parametrize("theta,shape", [(90.0, (16, 18, 20)), (150.0, (16, 18, 20)),
+                                         (120.0, (11, 17, 35))])
+def test_two_phase_3d_symmetry_planes_fp64(oracle_lib, theta, shape):
     """Symmetry planes on all four x and y faces (the quarter domains of
     Sections 3.6-3.7), wetting z walls, gravity along z: parity with the
-    oracle at 1e-12."""
-    shape, bc = (16, 18, 20), [4, 4, 4, 4, 1, 1]
+    oracle at 1e-12 (also with odd ny and a second x tile)."""
+    bc = [4, 4, 4, 4, 1, 1]
     st = _quarter_state(shape)
     ref, got = run_both(oracle_lib, shape, st, 60, nu=0.1, bc=bc, two_phase=True, sigma=1e-2,
                         W=4.0, M=0.3, theta_deg=theta, g=(0.0, 0.0, -1e-5), dt=0.5)
@@ -242,10 +245,10 @@ def test_two_phase_3d_symmetry_planes_fp32(oracle_lib):
         assert rel_l2(got[k], ref[k]) < 1e-4
 
 
-def test_symmetry_planes_equal_doubled_box_on_gpu():
+@pytest.mark.parametrize("shape", [(12, 14, 16), (10, 19, 13)])
+def test_symmetry_planes_equal_doubled_box_on_gpu(shape):
     """On the GPU too, the quarter domain with symmetry planes equals the
     periodic box of twice the size holding the mirror-symmetric fields."""
-    shape = (12, 14, 16)
     nz, ny, nx = shape
     st = _quarter_state(shape, walls=True)
 
