@@ -63,7 +63,7 @@ enum { K_MIRROR = 0, K_WET = 1 };
 // values are shared-memory reads and each value comes from memory about
 // once per plane.
 #ifndef ACM_TP3D_ZCH
-#define ACM_TP3D_ZCH 8
+#define ACM_TP3D_ZCH 6
 #endif
 constexpr int BX = 32, BY = 8, NT = BX * BY, TR = 2 * BY, ZCH = ACM_TP3D_ZCH;
 constexpr int WX = BX + 2, WY = TR + 2, WP = WX * WY;
