@@ -79,6 +79,10 @@ acm_status fail(acm_handle *h, acm_status st, const std::string &msg)
 
 acm_status cuda_fail(acm_handle *h, cudaError_t e, const char *what)
 {
+    // a failed runtime call stays the thread's last error; clear it, so that a
+    // non-sticky failure (an allocation that did not fit) is not reported
+    // again by the next launch on a context that is still usable
+    (void)cudaGetLastError();
     return fail(h, e == cudaErrorMemoryAllocation ? ACM_ENOMEM : ACM_ECUDA,
                 std::string(what) + ": " + cudaGetErrorString(e));
 }
@@ -921,8 +925,11 @@ acm_status acm_autotune(acm_handle *h, int nsteps, double *best_ms_per_step)
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     double best = 1e300;
     Cand bestc = {keep.t3y, keep.zchunks, keep.blocks, keep.line2d};
-    if (st == ACM_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
-        st = fail(h, ACM_ECUDA, "cudaEventCreate failed");
+    if (st == ACM_OK) {
+        cudaError_t ee = cudaEventCreate(&e0);
+        if (ee == cudaSuccess) ee = cudaEventCreate(&e1);
+        if (ee != cudaSuccess) st = cuda_fail(h, ee, "cudaEventCreate");
+    }
     for (size_t i = 0; i < cands.size() && st == ACM_OK; ++i) {
         const Cand &c = cands[i];
         if (h->dim == 3 && c.t3y != h->tune.t3y) {

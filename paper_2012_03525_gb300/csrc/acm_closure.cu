@@ -759,9 +759,11 @@ acm_status cfail(acm_closure *c, acm_status st, const std::string &m)
 #define CKC(c, call)                                                                        \
     do {                                                                                    \
         cudaError_t e_ = (call);                                                            \
-        if (e_ != cudaSuccess)                                                              \
+        if (e_ != cudaSuccess) {                                                            \
+            (void)cudaGetLastError(); /* a non-sticky failure must not outlive this call */ \
             return cfail((c), e_ == cudaErrorMemoryAllocation ? ACM_ENOMEM : ACM_ECUDA,      \
                          std::string(#call) + ": " + cudaGetErrorString(e_));               \
+        }                                                                                   \
     } while (0)
 
 size_t n_params()
@@ -936,6 +938,7 @@ acm_status acm_closure_create(int nx, int ny, int batch, acm_closure **out)
     al((void **)&c->derr, sizeof(unsigned));
     al((void **)&c->xnoisy, NB * 3 * 4);
     if (e != cudaSuccess) {
+        (void)cudaGetLastError();  // a failed allocation must not outlive this call
         release(c);
         delete c;
         return cfail(nullptr, e == cudaErrorMemoryAllocation ? ACM_ENOMEM : ACM_ECUDA,

@@ -82,13 +82,12 @@ extern "C" acm_status acm_reduce_mass_noalloc(int dim, int nx, int ny, int nz, i
         if (!g_partials_dev[dev]) {
             void *p = nullptr, *q = nullptr;
             e = cudaGetSymbolAddress(&p, g_partials);
-            if (e != cudaSuccess)
+            if (e == cudaSuccess) e = cudaGetSymbolAddress(&q, g_run);
+            if (e != cudaSuccess) {
+                (void)cudaGetLastError();  // the failure must not outlive this call
                 return noalloc_fail(ACM_ECUDA, std::string("cudaGetSymbolAddress: ") +
                                                    cudaGetErrorString(e));
-            e = cudaGetSymbolAddress(&q, g_run);
-            if (e != cudaSuccess)
-                return noalloc_fail(ACM_ECUDA, std::string("cudaGetSymbolAddress: ") +
-                                                   cudaGetErrorString(e));
+            }
             g_run_dev[dev] = static_cast<acm::RunDesc *>(q);
             g_partials_dev[dev] = static_cast<double *>(p);
         }

@@ -7,7 +7,10 @@
   nothing hidden.
 * Fault injection on the host: a non-finite value in the initial state is
   reported as ACM_EUNSTABLE by the next synchronising call, further steps
-  are refused, and a clean set_fields clears the error; a handle survives."""
+  are refused, and a clean set_fields clears the error; a handle survives.
+* Allocation failure: a grid larger than the device is refused with
+  ACM_ENOMEM on its first allocation, and later handles step normally (the
+  failed call does not linger as the runtime's last error)."""
 import numpy as np
 import pytest
 
@@ -97,3 +100,28 @@ def test_nan_in_initial_state_is_reported_and_cleared(shape):
         s.step(5)
         s.sync()
         assert np.isfinite(s.fields()[1]).all()
+
+
+def test_allocation_failure_leaves_the_context_usable():
+    """A grid larger than the whole device (a periodic 4000^3 FP64 box: one
+    field pool alone is about 514 GB) fails on its first allocation, before
+    anything is held, with ACM_ENOMEM; the failed allocation does not linger
+    as the runtime's last error, so handles created afterwards step and
+    synchronise normally (and agree with each other bit for bit)."""
+    with pytest.raises(acm.AcmError) as e:
+        acm.Solver(acm.make_params((4000, 4000, 4000)))
+    assert e.value.status in (acm.ENOMEM, acm.ECUDA)
+    assert "cudaMalloc" in str(e.value)
+    shape, kw = (12, 16, 32), dict(nu=0.04)
+    st = _state(shape, kw)
+    out = []
+    for _ in range(2):
+        with acm.Solver(acm.make_params(shape, **kw)) as s:
+            s.set_fields(*st)
+            s.step(10)
+            s.sync()
+            out.append(s.fields())
+    for a, b in zip(out[0], out[1]):
+        if a is not None:
+            assert np.isfinite(a).all()
+            assert np.array_equal(a, b)
