@@ -131,7 +131,10 @@ enum { ACM_SCHEME_SMAMES = 0, ACM_SCHEME_MAMES = 1 };
  * double-buffered device fields on the current CUDA device and returns the
  * handle in *out (NULL on failure).  The handle creates its own non-blocking
  * CUDA stream (replace it with acm_set_stream).  Fields are undefined until
- * acm_set_fields. */
+ * acm_set_fields.  A grid that does not fit in device memory returns
+ * ACM_ENOMEM with everything it allocated released; the failed allocation is
+ * not left behind as the CUDA runtime's last error, so the context stays
+ * usable for other handles. */
 acm_status acm_create(const acm_params *params, acm_handle **out);
 
 /* Elements of the precision's type (double for ACM_FP64, float for
