@@ -49,6 +49,10 @@ def test_params_struct_layout_matches_header():
 
 
 @pytest.mark.parametrize("kw,msg", [
+    (dict(shape=(8, 0)), "grid sizes must be >= 1"),     # empty grids
+    (dict(shape=(0, 8)), "grid sizes must be >= 1"),
+    (dict(shape=(0, 8, 8)), "grid sizes must be >= 1"),
+    (dict(shape=(8, 8, 0)), "grid sizes must be >= 1"),
     (dict(shape=(8, 8), dt=0.0), "dt"),
     (dict(shape=(8, 8), nu=-1.0), "nu"),
     (dict(shape=(8, 8), bc=[1, 0, 0, 0, 0, 0]), "periodic"),
@@ -83,6 +87,14 @@ def test_invalid_params_rejected_on_host(lib, kw, msg):
     assert st == acm.EINVAL
     assert not h.value
     assert msg in lib.acm_last_error(None).decode()
+
+
+def test_empty_batch_rejected(lib):
+    arr = (acm.Params * 1)(acm.make_params((8, 8)))
+    h = ctypes.c_void_p()
+    assert lib.acm_batch_create(arr, 0, ctypes.byref(h)) == acm.EINVAL
+    assert not h.value
+    assert "nruns < 1" in lib.acm_last_error(None).decode()
 
 
 def test_batch_must_share_precision(lib):
