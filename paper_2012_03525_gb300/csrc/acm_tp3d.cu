@@ -69,10 +69,11 @@ constexpr int BX = 32, BY = 8, NT = BX * BY, TR = 2 * BY, ZCH = ACM_TP3D_ZCH;
 constexpr int WX = BX + 2, WY = TR + 2, WP = WX * WY;
 constexpr int NLD = (WP + NT - 1) / NT;  // window elements a thread copies
 
-// index c in [-1, n + BX] wrapped into [0, n) (a full modulo only for grids
-// narrower than a tile), or reflected across the symmetry planes through
-// nodes 0 and n - 1 (positions beyond n belong to no node of the grid and
-// only need a valid index); *refl: c was reflected (odd fields change sign)
+// index c in [-1, n + BX] (x) or [-1, n + TR] (y) wrapped into [0, n) (a
+// full modulo only for grids narrower than a tile), or reflected across the
+// symmetry planes through nodes 0 and n - 1 (positions beyond n belong to no
+// node of the grid and only need a valid index); *refl: c was reflected (odd
+// fields change sign)
 __device__ __forceinline__ int wrapc(int c, int n, bool mirror, bool *refl)
 {
     if (mirror) {
@@ -116,7 +117,8 @@ struct WinXY {
             fy |= has[k] && ry[k];
         }
     }
-    // element k exists for every thread (a compile-time fact for full rounds)
+    // element k exists for this thread (in the full rounds, for every thread:
+    // a compile-time fact)
     __device__ __forceinline__ bool in(int k) const { return (k + 1) * NT <= WP || has[k]; }
 };
 
