@@ -204,7 +204,10 @@ acm_status acm_stability_ratio(const acm_params *params, const double *u, const 
 acm_status acm_batch_create(const acm_params *params, int nruns, acm_handle **out);
 
 /* Use this CUDA stream (a cudaStream_t, may be NULL for the legacy default
- * stream) for every later call on the handle.  Invalidates captured graphs. */
+ * stream) for every later call on the handle.  Invalidates captured graphs.
+ * Work already queued on the previous stream runs first: the handle's own
+ * stream is synchronised and destroyed; a caller's stream is ordered before
+ * the new one on the device (an event, no host wait). */
 acm_status acm_set_stream(acm_handle *h, void *stream);
 
 /* Number of runs in the handle (1 for acm_create). */
@@ -352,6 +355,9 @@ typedef struct acm_closure acm_closure;
 size_t acm_closure_num_params(void);
 /* grid nx x ny (both multiples of 16), BATCH states per call */
 acm_status acm_closure_create(int nx, int ny, int batch, acm_closure **out);
+/* later calls run on this stream (NULL: the legacy default stream, the
+ * initial one); work already queued on the previous stream is ordered before
+ * it on the device (an event, no host wait) */
 acm_status acm_closure_set_stream(acm_closure *c, void *stream);
 /* normalisation scales s_rho, s_u, s_u (s_u shared by u and v) */
 acm_status acm_closure_set_scales(acm_closure *c, const float *scales3);

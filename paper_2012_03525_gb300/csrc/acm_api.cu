@@ -727,6 +727,18 @@ cudaError_t restrict_launch(acm_handle *f, acm_handle *c, int factor, double us,
 }  // namespace
 
 namespace acm {
+cudaError_t order_streams(cudaStream_t prev, cudaStream_t next)
+{
+    if (prev == next) return cudaSuccess;
+    cudaEvent_t ev = nullptr;
+    cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+    e = cudaEventRecord(ev, prev);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(next, ev, 0);
+    cudaEventDestroy(ev);  // released once the wait has been satisfied
+    return e;
+}
+
 acm_status handle_fields_f32(acm_handle *h, int run, float **r, float **u, float **v, int *nx,
                              int *ny)
 {
@@ -810,13 +822,18 @@ acm_status acm_stability_ratio(const acm_params *params, const double *u, const 
 acm_status acm_set_stream(acm_handle *h, void *stream)
 {
     if (!h) return fail(nullptr, ACM_EINVAL, "null handle");
+    const cudaStream_t next = static_cast<cudaStream_t>(stream);
+    CK(h, cudaSetDevice(h->device));
     drop_graph(h);
     if (h->own_stream && h->stream) {
         cudaStreamSynchronize(h->stream);
         cudaStreamDestroy(h->stream);
+    } else {
+        // a caller's stream: the work already queued on it comes first
+        CK(h, order_streams(h->stream, next));
     }
     h->own_stream = false;
-    h->stream = static_cast<cudaStream_t>(stream);
+    h->stream = next;
     return ACM_OK;
 }
 

@@ -951,7 +951,10 @@ acm_status acm_closure_create(int nx, int ny, int batch, acm_closure **out)
 acm_status acm_closure_set_stream(acm_closure *c, void *stream)
 {
     if (!c) return cfail(nullptr, ACM_EINVAL, "null closure");
-    c->stream = static_cast<cudaStream_t>(stream);
+    const cudaStream_t next = static_cast<cudaStream_t>(stream);
+    // the work already queued on the previous stream comes first
+    CKC(c, acm::order_streams(c->stream, next));
+    c->stream = next;
     return ACM_OK;
 }
 

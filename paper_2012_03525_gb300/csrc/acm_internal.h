@@ -179,4 +179,8 @@ cudaError_t launch_export(const T *src, double *dst, const RunDesc &run, int dim
 acm_status handle_fields_f32(acm_handle *h, int run, float **r, float **u, float **v, int *nx,
                              int *ny);
 
+// Make stream `next` wait, on the device, for the work queued so far on
+// stream `prev` (an event recorded on prev; no host wait).
+cudaError_t order_streams(cudaStream_t prev, cudaStream_t next);
+
 }  // namespace acm

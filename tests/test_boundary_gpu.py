@@ -200,3 +200,29 @@ def test_reduce_laplace_rejects_single_phase():
         with pytest.raises(acm.AcmError) as e:
             s.reduce_laplace()
         assert e.value.status == acm.EINVAL
+
+
+# ------------------------------------------------------------- acm_set_stream
+def test_stream_switch_keeps_queued_work_first(torch):
+    """A handle moved from one caller stream to another with steps still
+    queued on the first: those steps run before the ones queued on the
+    second (the library orders the streams on the device), so the result
+    is bit for bit one uninterrupted run."""
+    shape = (256, 512)
+    rng = np.random.default_rng(5)
+    st = [1 + 0.01 * _smooth(rng, shape), 0.02 * _smooth(rng, shape), 0.02 * _smooth(rng, shape)]
+    p = acm.make_params(shape, nu=0.05, precision=acm.FP32_DEV)
+    with acm.Solver(p) as s:
+        s.set_fields(*st)
+        s.step(600)
+        want = s.fields()
+    a, b = torch.cuda.Stream(), torch.cuda.Stream()
+    with acm.Solver(p) as s:
+        s.set_stream(a.cuda_stream)
+        s.set_fields(*st)
+        s.step(300)
+        s.set_stream(b.cuda_stream)  # no host wait in between
+        s.step(300)
+        got = s.fields()
+    for k in range(3):
+        np.testing.assert_array_equal(got[k], want[k])
