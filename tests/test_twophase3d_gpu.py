@@ -306,3 +306,30 @@ def test_drop_jumping_quarter_domain_section_3_7():
     assert zc[-1] > 1.15 and np.all(np.diff(zc[3:]) > 0)
     assert np.abs(c32[:, 0] - wd).max() < 2e-3
     assert np.abs(c32[:, 1] - zc).max() < 2e-3
+
+
+def test_drop_jumping_full_size_two_steps(oracle_lib):
+    """The benchmark's 3D two-phase workload at its full size (the Section
+    3.7 quarter domain, 120 x 120 x 200 with symmetry planes and theta = 180
+    walls, Oh = 0.037), in the kernels and launch configuration the
+    benchmark times: two steps of the whole grid against the oracle, FP64 at
+    1e-12 and FP32 deviation storage at the FP32 bounds of the small cases."""
+    from paper_2012_03525_gb300 import workloads as wl
+    case = wl.DropJumping(0.037)
+    init = list(case.initial())
+    kw = dict(dt=1.0, nu=case.nu, bc=list(case.bc), two_phase=True, sigma=case.sigma, W=case.W,
+              M=case.M, theta_deg=case.theta_deg)
+    ref = [x.copy() for x in init]
+    oracle_lib.step(oracle_lib.make_params(case.shape, **kw), *ref, nsteps=2)
+    for prec in (acm.FP64, acm.FP32_DEV):
+        with acm.Solver(acm.make_params(case.shape, precision=prec, **kw)) as s:
+            s.set_fields(*init)
+            s.step(2)
+            got = list(s.fields())
+        if prec == acm.FP64:
+            assert_parity(ref, got)
+        else:
+            assert rel_l2(got[4], ref[4]) < 1e-6
+            for k in (1, 2, 3):
+                assert rel_l2(got[k], ref[k]) < 1e-4
+            assert rel_l2(got[0] - 1, ref[0] - 1) < 1e-3
