@@ -221,3 +221,70 @@ def test_line2d_tp_matches_tile_kernel_fp32():
     assert rel_l2(out[0][4], out[1][4]) < 1e-6
     for k in (1, 2):
         assert rel_l2(out[0][k], out[1][k]) < 1e-4
+
+
+# ------------------------------------------- the measured workloads, full size
+def test_line2d_tgv4096_full_size(oracle_lib):
+    """The 4096^2 TGV of the 2D throughput measurement (u0 = 0.05, nu =
+    0.01) at full size on the line kernel, whose items are 32 rows long
+    there (smaller grids get shorter ones): two steps against the oracle,
+    FP32 deviation storage (the measured form) at the FP32 bounds and FP64
+    at 1e-12."""
+    n = 4096
+    st = list(wl.tgv2d(n, 0.05))
+    ref = [x.copy() for x in st]
+    oracle_lib.step(oracle_lib.make_params((n, n), nu=0.01), *ref, nsteps=2)
+    ref = ref + [None, None]
+    for prec in (acm.FP32_DEV, acm.FP64):
+        with acm.Solver(acm.make_params((n, n), nu=0.01, precision=prec)) as s:
+            s.set_tuning(acm.TUNE_LINE2D, 1)
+            s.set_fields(*st)
+            s.step(2)
+            got = list(s.fields())
+        if prec == acm.FP64:
+            assert_parity(ref, got)
+        else:
+            assert_parity(ref, got, tol=2e-5, tol_rho=1e-4)
+
+
+@pytest.mark.parametrize("prec", [acm.FP64, acm.FP32_DEV])
+def test_line2d_tp_full_drop_batch_sampled(oracle_lib, prec):
+    """The whole 512-run batched-drop workload in one handle on the two-phase
+    line kernel, in the launch configuration the measurement times (with
+    this many runs its items are 64 rows long): after 4 steps, six sampled
+    runs (the four largest grids and the two smallest, each given a smooth
+    flow) equal their oracle runs, FP64 at 1e-12 and FP32 at the FP32
+    bounds of the small cases."""
+    co = oracle_lib
+    spec = wl.batch_drops()
+    order = np.argsort([d.n for d in spec])
+    pick = [int(i) for i in list(order[-4:]) + list(order[:2])]
+    rng = np.random.default_rng(12)
+    states = []
+    for i, d in enumerate(spec):
+        rho, u, v, phi = wl.drop2d(d.n, d.radius, d.W, eps=d.eps)
+        if i in pick:
+            u, v = u + _flow(rng, u.shape), v + _flow(rng, v.shape)
+        states.append([rho, u, v, phi])
+    params = [acm.make_params((d.n, d.n), nu=d.nu, two_phase=True, sigma=d.sigma, W=d.W, M=d.M,
+                              precision=prec) for d in spec]
+    steps = 4
+    with acm.Solver(params) as s:
+        s.set_tuning(acm.TUNE_LINE2D, 1)
+        for r, st in enumerate(states):
+            s.set_fields(st[0], st[1], st[2], None, st[3], run=r)
+        s.step(steps)
+        got = {i: list(s.fields(run=i)) for i in pick}
+    for i in pick:
+        d = spec[i]
+        st = [x.copy() for x in states[i]]
+        co.step(co.make_params((d.n, d.n), nu=d.nu, two_phase=True, sigma=d.sigma, W=d.W, M=d.M),
+                st[0], st[1], st[2], None, st[3], nsteps=steps)
+        ref = [st[0], st[1], st[2], None, st[3]]
+        if prec == acm.FP64:
+            assert_parity(ref, got[i])
+        else:
+            assert rel_l2(got[i][4], ref[4]) < 1e-6
+            for k in (1, 2):
+                assert rel_l2(got[i][k], ref[k]) < 1e-4
+            assert rel_l2(got[i][0] - 1, ref[0] - 1) < 1e-3
